@@ -1,0 +1,313 @@
+"""CPU oracle for the super-droplet hot path (libcloudph++ 0.2, Sec. 5).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s ``cpu_baseline`` / reference
+legs may import this package.  It wraps the plain serial C99 oracle in
+``sdm_oracle.c`` (double precision, ``-ffp-contract=off``) with ctypes and
+numpy; it shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = [os.path.join(_HERE, f) for f in ("sdm_oracle.c", "philox.c")]
+_lock = threading.Lock()
+_lib = None
+
+MAX_MODES = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + [os.path.join(_HERE, "sdm_oracle.h")])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Mode(C.Structure):
+    _fields_ = [("rm", C.c_double), ("sigma", C.c_double), ("n_stp", C.c_double), ("kappa", C.c_double)]
+
+
+class Domain(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
+        ("sd_conc", C.c_int), ("kernel", C.c_int), ("golovin_b", C.c_double),
+        ("init_dist", C.c_int), ("exp_mean_volume", C.c_double), ("exp_n0", C.c_double),
+        ("n_modes", C.c_int), ("modes", Mode * MAX_MODES),
+        ("seed", C.c_uint64), ("physics", C.c_int),
+    ]
+
+
+class Opts(C.Structure):
+    _fields_ = [
+        ("adve", C.c_int), ("sedi", C.c_int), ("cond", C.c_int), ("coal", C.c_int),
+        ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n_pairs", C.c_uint64), ("n_coll", C.c_uint64), ("n_pgt1", C.c_uint64),
+        ("n_recycled", C.c_uint64), ("n_euler", C.c_uint64), ("n_bisect", C.c_uint64),
+        ("max_p", C.c_double), ("rainfall", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SDs(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("uid", C.POINTER(C.c_uint64)), ("N", C.POINTER(C.c_uint64)),
+        ("rw2", C.POINTER(C.c_double)), ("rd3", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_double)),
+        ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)), ("z", C.POINTER(C.c_double)),
+    ]
+
+
+class Thermo(C.Structure):
+    _fields_ = [(k, C.c_double) for k in (
+        "th", "rv", "rhod", "T", "p", "lv", "rho_v", "rho_vs", "rho_v_eff", "dth_drv", "A", "Dterm",
+        "rho_a", "mu", "nu", "lambda_D", "lambda_K", "Sc", "Pr", "cX")]
+
+
+_P = C.POINTER
+_D = C.c_double
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_philox4x64_10.argtypes = [_P(C.c_uint64), _P(C.c_uint64), _P(C.c_uint64)]
+            L.orc_u01.argtypes = [C.c_uint64]; L.orc_u01.restype = _D
+            L.orc_n_cells.argtypes = [_P(Domain)]; L.orc_n_cells.restype = C.c_int64
+            L.orc_n_groups.argtypes = [_P(Domain)]; L.orc_n_groups.restype = C.c_int
+            L.orc_cell_of.argtypes = [_P(Domain), _D, _D, _D]; L.orc_cell_of.restype = C.c_int64
+            L.orc_thermo_eval.argtypes = [_D, _D, _D, _D, _P(Thermo)]
+            L.orc_reynolds.argtypes = [_D, _P(Thermo)]; L.orc_reynolds.restype = _D
+            L.orc_vterm.argtypes = [_D, _P(Thermo)]; L.orc_vterm.restype = _D
+            L.orc_growth.argtypes = [_D, _D, _D, _P(Thermo), C.c_int]; L.orc_growth.restype = _D
+            L.orc_solve_rw2.argtypes = [_D, _D, _D, _P(Thermo), _D, C.c_int, _P(Stats)]
+            L.orc_solve_rw2.restype = _D
+            L.orc_equilibrium_rw2.argtypes = [_D, _D, _D, _D]; L.orc_equilibrium_rw2.restype = _D
+            L.orc_rd_range.argtypes = [_P(Domain), C.c_int, _P(_D), _P(_D)]; L.orc_rd_range.restype = C.c_int
+            L.orc_init_cells.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), C.c_int64, _P(C.c_int64), _P(SDs)]
+            L.orc_init_cells.restype = C.c_int
+            L.orc_condense.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), _P(Stats)]
+            L.orc_recycle.argtypes = [_P(SDs), _P(Stats)]
+            L.orc_advect.argtypes = [_P(Domain), _P(SDs), _P(_D), _P(_D), _P(_D), _P(_D)]
+            L.orc_transport.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D),
+                                        _P(_D), _P(_D), _P(_D), _P(Stats)]
+            L.orc_coalesce.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), C.c_uint64, _P(Stats)]
+            L.orc_step_sync.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), _P(Stats)]
+            L.orc_step_async.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D),
+                                         _P(_D), _P(_D), _P(_D), C.c_uint64, _P(Stats)]
+            L.orc_moments.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _D, _D, C.c_int, _P(_D)]
+            L.orc_sd_conc.argtypes = [_P(Domain), _P(SDs), _P(_D)]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P(_D))
+
+
+# ---------------------------------------------------------------------------
+def philox(ctr, key):
+    """Philox4x64-10 of one 256-bit counter under one 128-bit key."""
+    c = (C.c_uint64 * 4)(*[int(v) for v in ctr])
+    k = (C.c_uint64 * 2)(*[int(v) for v in key])
+    o = (C.c_uint64 * 4)()
+    lib().orc_philox4x64_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def u01(v):
+    return lib().orc_u01(C.c_uint64(int(v)))
+
+
+def make_domain(cfg: dict) -> Domain:
+    """Build the oracle's domain struct from a plain workload dict."""
+    d = Domain()
+    d.nx, d.ny, d.nz = cfg.get("nx", 0), cfg.get("ny", 0), cfg.get("nz", 0)
+    d.dx, d.dy, d.dz = cfg.get("dx", 1.0), cfg.get("dy", 1.0), cfg.get("dz", 1.0)
+    d.dt = cfg.get("dt", 1.0)
+    d.sd_conc = cfg.get("sd_conc", 64)
+    d.kernel = {"geometric": 0, "golovin": 1}[cfg.get("kernel", "geometric")]
+    d.golovin_b = cfg.get("golovin_b", 0.0)
+    d.init_dist = {"lognormal": 0, "exponential": 1}[cfg.get("init_dist", "lognormal")]
+    d.exp_mean_volume = cfg.get("exp_mean_volume", 0.0)
+    d.exp_n0 = cfg.get("exp_n0", 0.0)
+    modes = cfg.get("modes", [])
+    d.n_modes = len(modes)
+    for i, m in enumerate(modes):
+        d.modes[i] = Mode(m["rm"], m["sigma"], m["n_stp"], m["kappa"])
+    d.seed = cfg.get("seed", 0)
+    d.physics = cfg.get("physics", 1)
+    return d
+
+
+def make_opts(o: dict | None = None) -> Opts:
+    o = o or {}
+    return Opts(o.get("adve", 1), o.get("sedi", 1), o.get("cond", 1), o.get("coal", 1),
+                o.get("RH_max", 44.0), o.get("sstp_cond", 10), o.get("sstp_coal", 10))
+
+
+def thermo(th, rv, rhod, RH_max=44.0) -> Thermo:
+    t = Thermo()
+    lib().orc_thermo_eval(th, rv, rhod, RH_max, C.byref(t))
+    return t
+
+
+class State:
+    """Super-droplet arrays held as numpy (structure of arrays)."""
+
+    FIELDS = ("uid", "N", "rw2", "rd3", "kappa", "x", "y", "z")
+
+    def __init__(self, n: int):
+        self.uid = np.zeros(n, np.uint64)
+        self.N = np.zeros(n, np.uint64)
+        for f in ("rw2", "rd3", "kappa", "x", "y", "z"):
+            setattr(self, f, np.zeros(n, np.float64))
+        self._n = n
+
+    @property
+    def n(self):
+        return self._n
+
+    def copy(self) -> "State":
+        s = State(self._n)
+        for f in self.FIELDS:
+            getattr(s, f)[:] = getattr(self, f)
+        return s
+
+    def subset(self, mask) -> "State":
+        idx = np.nonzero(mask)[0]
+        s = State(len(idx))
+        for f in self.FIELDS:
+            getattr(s, f)[:] = getattr(self, f)[idx]
+        return s
+
+    def struct(self) -> SDs:
+        s = SDs()
+        s.n = self._n
+        s.uid = self.uid.ctypes.data_as(_P(C.c_uint64))
+        s.N = self.N.ctypes.data_as(_P(C.c_uint64))
+        for f in ("rw2", "rd3", "kappa", "x", "y", "z"):
+            setattr(s, f, getattr(self, f).ctypes.data_as(_P(_D)))
+        return s
+
+    def sorted_by_uid(self) -> "State":
+        o = np.argsort(self.uid, kind="stable")
+        s = State(self._n)
+        for f in self.FIELDS:
+            getattr(s, f)[:] = getattr(self, f)[o]
+        return s
+
+
+class Oracle:
+    """One simulated domain advanced by the oracle, following the paper's
+    calling sequence (Sec. 5.2.2): init, then step_sync / step_async pairs."""
+
+    def __init__(self, cfg: dict):
+        self.cfg = dict(cfg)
+        self.dom = make_domain(cfg)
+        L = lib()
+        self.n_cells = int(L.orc_n_cells(C.byref(self.dom)))
+        self.n_groups = int(L.orc_n_groups(C.byref(self.dom)))
+        self.step_index = 0
+        self.stats = Stats()
+        self.state: State | None = None
+
+    def rd_range(self, group=0):
+        lo, hi = _D(), _D()
+        rc = lib().orc_rd_range(C.byref(self.dom), group, C.byref(lo), C.byref(hi))
+        if rc != 0:
+            raise RuntimeError(f"orc_rd_range failed ({rc})")
+        return lo.value, hi.value
+
+    def init_cells(self, th, rv, rhod, cells) -> State:
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        n = len(cells) * self.n_groups * self.dom.sd_conc
+        st = State(n)
+        s = st.struct()
+        rc = lib().orc_init_cells(C.byref(self.dom), _dp(th), _dp(rv), _dp(rhod), len(cells),
+                                  cells.ctypes.data_as(_P(C.c_int64)), C.byref(s))
+        if rc != 0:
+            raise RuntimeError(f"orc_init_cells failed ({rc})")
+        return st
+
+    def init(self, th, rv, rhod):
+        self.th = np.array(th, np.float64).ravel().copy()
+        self.rv = np.array(rv, np.float64).ravel().copy()
+        self.rhod = np.array(rhod, np.float64).ravel().copy()
+        self.state = self.init_cells(self.th, self.rv, self.rhod, np.arange(self.n_cells))
+        return self.state
+
+    def step_sync(self, opts: dict | None = None):
+        o = make_opts(opts)
+        s = self.state.struct()
+        lib().orc_step_sync(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
+                            _dp(self.rhod), C.byref(self.stats))
+
+    def step_async(self, opts: dict | None = None, rhoCx=None, rhoCy=None, rhoCz=None):
+        o = make_opts(opts)
+        s = self.state.struct()
+        lib().orc_step_async(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
+                             _dp(self.rhod), _dp(rhoCx), _dp(rhoCy), _dp(rhoCz),
+                             self.step_index, C.byref(self.stats))
+        self.step_index += 1
+
+    def moments(self, wet: bool, r_min: float, r_max: float, k: int):
+        out = np.zeros(self.n_cells)
+        s = self.state.struct()
+        lib().orc_moments(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), r_min, r_max, k, _dp(out))
+        return out
+
+    def sd_conc(self):
+        out = np.zeros(self.n_cells)
+        s = self.state.struct()
+        lib().orc_sd_conc(C.byref(self.dom), C.byref(s), _dp(out))
+        return out
+
+
+def solve_rw2(x0, rd3, kappa, t: Thermo, dtp, physics=1):
+    st = Stats()
+    x = lib().orc_solve_rw2(x0, rd3, kappa, C.byref(t), dtp, physics, C.byref(st))
+    return x, st
+
+
+def growth(x, rd3, kappa, t: Thermo, physics=1):
+    return lib().orc_growth(x, rd3, kappa, C.byref(t), physics)
+
+
+def vterm(rw2, t: Thermo):
+    return lib().orc_vterm(rw2, C.byref(t))
+
+
+def reynolds(rw2, t: Thermo):
+    return lib().orc_reynolds(rw2, C.byref(t))
+
+
+def equilibrium_rw2(rd3, kappa, RH, T):
+    return lib().orc_equilibrium_rw2(rd3, kappa, RH, T)

@@ -1,0 +1,206 @@
+"""Pins of the oracle's Monte-Carlo coalescence (paper Sec. 5.1.4, eq. P_ij)
+against results fixed by mathematics rather than by the oracle itself:
+
+* the Golovin (1963) analytic solution of the coalescence equation for an
+  exponential initial spectrum (number moment and mass density);
+* the unbiasedness identity implied by eq. (P_ij): with all P <= 1, the
+  expected loss of droplets per substep is sum_{i<j} N_i N_j K_ij dt/dV;
+* uniformity of the random pairing over all perfect matchings;
+* exact conservation of sum N r^3 and the integer multiplicity bookkeeping.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy.special import i1e
+from scipy.stats import chi2
+
+import oracle
+import workloads
+from oracle_helpers import box_cfg, coalesce, make_state
+
+
+# ---------------------------------------------------------------------------
+# pairing: every perfect matching of the n super-droplets is equally likely
+def _matching_of(state_before, state_after):
+    """Recover which super-droplets merged.  Radii cubes are distinct powers
+    of two, so the merged r^3 of each small partner names the large one."""
+    r3b = state_before.rw2 ** 1.5
+    r3a = state_after.rw2 ** 1.5
+    pairs = []
+    for i in range(len(r3b)):
+        extra = r3a[i] - r3b[i]
+        if extra > 0.5 * r3b.min():
+            j = int(np.argmin(np.abs(r3b - extra)))
+            pairs.append(tuple(sorted((i, j))))
+    return tuple(sorted(pairs))
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_pairing_uniform_over_matchings(n):
+    cfg = box_cfg(n_sd=n, b=1e30)  # P >> 1: every pair collides
+    N = np.array([10 ** (n - i) for i in range(n)])  # distinct: roles fixed
+    rw2 = (2.0 ** np.arange(n)) ** (2.0 / 3.0) * 1e-12
+    counts = {}
+    trials = 3000
+    for step in range(trials):
+        s0 = make_state(N, rw2)
+        s1 = s0.copy()
+        coalesce(cfg, s1, step=step)
+        m = _matching_of(s0, s1)
+        counts[m] = counts.get(m, 0) + 1
+    # number of ways to choose floor(n/2) disjoint pairs
+    k = n // 2
+    n_match = math.factorial(n) // (math.factorial(n - 2 * k) * 2 ** k * math.factorial(k))
+    assert len(counts) == n_match
+    for m in counts:
+        assert len(m) == k
+    obs = np.array(list(counts.values()), float)
+    stat = ((obs - trials / n_match) ** 2 / (trials / n_match)).sum()
+    assert stat < chi2.ppf(0.9999, n_match - 1)
+
+
+# ---------------------------------------------------------------------------
+# unbiasedness of the scaled probability (eq. P_ij)
+@pytest.mark.parametrize("n,seed", [(2, 0), (3, 1), (5, 2), (6, 3)])
+def test_expected_droplet_loss_matches_all_pairs_sum(n, seed):
+    rng = np.random.default_rng(seed)
+    N = rng.integers(50, 5000, size=n)
+    rw2 = (rng.uniform(5e-6, 30e-6, size=n)) ** 2
+    V = 4.0 / 3.0 * math.pi * rw2 ** 1.5
+    dV, dt = 1.0, 1.0
+    # choose b so that the largest scaled P is 0.8
+    k = n // 2
+    scale = n * (n - 1) / (2 * k)
+    Kmax = max(max(N[i], N[j]) * (V[i] + V[j]) for i, j in itertools.combinations(range(n), 2))
+    b = 0.8 / (Kmax * dt / dV * scale)
+    cfg = box_cfg(n_sd=n, b=b, dV=dV, dt=dt, seed=seed)
+    # brute force over all n(n-1)/2 pairs
+    expected = sum(N[i] * N[j] * b * (V[i] + V[j]) * dt / dV for i, j in itertools.combinations(range(n), 2))
+    trials = 20000
+    losses = np.empty(trials)
+    for step in range(trials):
+        s = make_state(N, rw2)
+        st = coalesce(cfg, s, step=step)
+        assert st.max_p <= 1.0
+        losses[step] = N.sum() - s.N.astype(np.int64).sum()
+    se = losses.std(ddof=1) / math.sqrt(trials)
+    assert abs(losses.mean() - expected) < 4.5 * se
+
+
+# ---------------------------------------------------------------------------
+# split / merge of one collision (Sec. 5.1.4): roles and exact integers
+def test_unequal_multiplicities_split_merge():
+    cfg = box_cfg(n_sd=2, b=1e30)
+    rd3 = np.array([2e-24, 3e-24])
+    s = make_state([7, 3], np.array([4e-12, 9e-12]), rd3=rd3, kappa=np.array([0.2, 1.2]))
+    coalesce(cfg, s, step=0)
+    # larger-N super-droplet keeps radii and loses the other's multiplicity
+    assert list(s.N) == [4, 3]
+    assert s.rw2[0] == 4e-12 and s.rd3[0] == 2e-24
+    # smaller-N super-droplet keeps N and takes the merged droplet
+    assert s.rw2[1] ** 1.5 == pytest.approx((4e-12) ** 1.5 + (9e-12) ** 1.5, rel=1e-14)
+    assert s.rd3[1] == pytest.approx(5e-24, rel=1e-15)
+    assert s.kappa[1] == pytest.approx((0.2 * 2 + 1.2 * 3) / 5, rel=1e-14)
+
+
+def test_equal_multiplicities_leave_a_zero():
+    cfg = box_cfg(n_sd=2, b=1e30)
+    s = make_state([5, 5], np.array([1e-12, 4e-12]))
+    coalesce(cfg, s, step=3)
+    assert sorted(s.N.tolist()) == [0, 5]
+    merged = int(np.nonzero(s.N)[0][0])
+    assert s.rw2[merged] ** 1.5 == pytest.approx(1e-18 + 8e-18, rel=1e-14)
+
+
+def test_zero_multiplicity_takes_no_part():
+    cfg = box_cfg(n_sd=3, b=1e30)
+    s = make_state([0, 4, 9], np.array([1e-12, 4e-12, 9e-12]))
+    st = coalesce(cfg, s, step=0)
+    assert st.n_pairs == 1 and st.n_coll == 1
+    assert s.N[0] == 0 and s.rw2[0] == 1e-12
+
+
+def test_invariants_geometric_kernel_many_events():
+    # many super-droplets in one cell, geometric kernel, 10 substeps
+    rng = np.random.default_rng(7)
+    n = 400
+    cfg = box_cfg(n_sd=n, kernel="geometric", dV=1e-3, dt=1.0, seed=7)
+    N = rng.integers(1, 10 ** 6, size=n)
+    rw2 = np.exp(rng.uniform(np.log(2e-6), np.log(400e-6), size=n)) ** 2
+    rd3 = np.exp(rng.uniform(np.log(1e-8), np.log(1e-7), size=n)) ** 3
+    s = make_state(N, rw2, rd3=rd3, kappa=np.full(n, 0.61))
+    m_w0 = (N * rw2 ** 1.5).sum()
+    m_d0 = (N * rd3).sum()
+    st = coalesce(cfg, s, step=11, sstp=10)
+    assert st.n_coll > 20
+    Na = s.N.astype(np.int64)
+    assert (Na >= 0).all()
+    assert Na.sum() < N.sum()
+    assert (Na * s.rw2 ** 1.5).sum() == pytest.approx(m_w0, rel=1e-13)
+    assert (Na * s.rd3).sum() == pytest.approx(m_d0, rel=1e-13)
+    np.testing.assert_allclose(s.kappa, 0.61, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Golovin (1963) analytic solution, box set-up of Shima et al. (2009)
+B, N0, RBAR, DV = 1500.0, 2.0 ** 23, 30.531e-6, 1e6
+VBAR = 4.0 / 3.0 * math.pi * RBAR ** 3
+
+
+def golovin_mass_density(r, t):
+    """Mass density per unit ln r [kg m^-3] of the analytic solution
+    n(V,t) = n0 (1-tau) / (V sqrt(tau)) exp(-(1+tau) V/Vbar) I1(2 V sqrt(tau)/Vbar),
+    tau = 1 - exp(-b n0 Vbar t)."""
+    V = 4.0 / 3.0 * math.pi * r ** 3
+    tau = 1.0 - math.exp(-B * N0 * VBAR * t)
+    x = 2.0 * V * math.sqrt(tau) / VBAR
+    n = N0 * (1 - tau) / (V * math.sqrt(tau)) * np.exp(-(1 + tau) * V / VBAR + x) * i1e(x)
+    return 3.0 * V * V * n * 1000.0
+
+
+@pytest.fixture(scope="module")
+def golovin_runs():
+    snaps = []
+    for seed in range(4):
+        w = workloads.golovin_box(seed=seed)
+        o = oracle.Oracle(w.cfg)
+        o.init(w.th, w.rv, w.rhod)
+        out = {}
+        for t in range(1, 1801):
+            o.step_async(w.opts)
+            if t % 600 == 0:
+                out[t] = (o.state.N.astype(float).copy(), o.state.rw2.copy())
+        snaps.append(out)
+    return snaps
+
+
+def test_golovin_number_moment(golovin_runs):
+    for t in (600, 1200, 1800):
+        m0 = np.mean([r[t][0].sum() / DV for r in golovin_runs])
+        assert m0 == pytest.approx(N0 * math.exp(-B * N0 * VBAR * t), rel=0.04)
+
+
+def test_golovin_mass_density(golovin_runs):
+    edges = np.linspace(math.log(10e-6), math.log(5e-3), 33)
+    mid = np.exp(0.5 * (edges[1:] + edges[:-1]))
+    for t in (1200, 1800):
+        hs = []
+        for r in golovin_runs:
+            N, rw2 = r[t]
+            rr = np.sqrt(rw2)
+            mass = N * 4.0 / 3.0 * math.pi * rr ** 3 * 1000.0 / DV
+            h, _ = np.histogram(np.log(rr), edges, weights=mass)
+            hs.append(h / np.diff(edges))
+        g = golovin_mass_density(mid, t)
+        sel = g > 0.1 * g.max()
+        hs = np.array(hs)
+        sem = hs.std(axis=0, ddof=1)[sel] / math.sqrt(len(hs))  # seed-to-seed error
+        dev = np.abs(hs.mean(axis=0)[sel] - g[sel])
+        assert sel.sum() >= 8
+        assert (dev <= 0.1 * g[sel] + 3.0 * sem).all()
+        assert (dev / g[sel]).mean() < 0.08
+    # total liquid water is conserved: n0 * Vbar * rho_w = 1 g m^-3
+    N, rw2 = golovin_runs[0][1800]
+    assert (N * 4.0 / 3.0 * math.pi * rw2 ** 1.5).sum() / DV == pytest.approx(N0 * VBAR, rel=0.03)
