@@ -1,0 +1,331 @@
+"""Benchmark of the super-droplet hot path (one full timestep = step_sync
+with sstp_cond condensation substeps + step_async with recycling,
+advection, sedimentation, regrouping and sstp_coal coalescence substeps).
+
+Default workload: the 2D prescribed-flow kinematic cloud, 75 x 75 cells of
+20 m, 64 super-droplets per cell (360 000), bimodal ammonium-sulphate
+aerosol, geometric kernel, dt = 1 s, 10/10 substeps, FP64 state.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  Metric: super-droplet-steps per second over all
+ranks.  ``value`` is device time (CUDA events on the library's stream, L2
+flushed between timed steps, inputs resident in HBM); ``e2e`` is the same
+metric through the public API with host buffers (theta and r_v copied in and
+out every step), wall clock.  Multi-GPU runs are independent replicas (one
+domain per rank, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "super-droplet-steps/s (coal+cond)"
+UNIT = "SD-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 arithmetic peak of one GB300 derived from unit counts and clocks:
+# 1.25 TFLOP/s nominal at the 2070 MHz boost clock over 152 SMs is 2 DFMA
+# (4 FP64 flops) per SM per clock
+FP64_FLOPS_PER_SM_CLK = 4.0
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="icmw_2d", choices=["icmw_2d", "updraft_3d", "golovin_box"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, seed: int):
+    if name == "icmw_2d":
+        return workloads.icmw_2d(seed=seed)
+    if name == "updraft_3d":
+        return workloads.updraft_3d(seed=seed)
+    return workloads.golovin_box(seed=seed)
+
+
+def workload_desc(w) -> dict:
+    c = w.cfg
+    d = dict(workload=f"{w.name}: {c['nx']}x{c['ny']}x{c['nz']} cells, {c['sd_conc']} SD/cell "
+                      f"({w.n_sd} SDs), sstp_cond={w.opts['sstp_cond']}, sstp_coal={w.opts['sstp_coal']}, "
+                      f"kernel={c['kernel']}, dt={c['dt']} s",
+             n_sd=w.n_sd, n_cells=w.n_cells, sd_per_cell=c["sd_conc"], processes="cond+adve+sedi+coal",
+             l2="flushed (256 MiB write) before every timed step")
+    return d
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank: int, world: int):
+    import torch
+
+    from paper_1310_1905_gb300 import sdm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    w = make_workload(args.workload, seed=rank)
+    opts = w.opts
+    if args.workload == "golovin_box":
+        opts = dict(w.opts)
+    th = torch.tensor(w.th, dtype=torch.float64, device="cuda")
+    rv = torch.tensor(w.rv, dtype=torch.float64, device="cuda")
+    rhod = torch.tensor(w.rhod, dtype=torch.float64, device="cuda")
+    Cs = [None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
+          for a in (w.rhoCx, w.rhoCy, w.rhoCz)]
+    p = sdm.Particles(w.cfg, th, rv, rhod, *Cs, stream=stream.cuda_stream, precision=args.precision)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        if opts.get("cond", 1):
+            p.step_sync(opts, th, rv)
+        p.step_async(opts)
+        p.wait()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    sdm.sdm_timing_enable(p.ctx, True)
+    sdm.sdm_get_timing(p.ctx, reset=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_dev = 0.0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    tim = sdm.sdm_get_timing(p.ctx, reset=True)
+    sdm.sdm_timing_enable(p.ctx, False)
+    t_max = dist_max(t_dev, world)
+    stats = p.stats()
+    res = dict(t_dev=t_max, timing=tim, clocks=clk, stats=stats, n_sd=p.n_sd, w=w)
+    # ---- e2e through the public API with host buffers
+    if not args.no_e2e:
+        th_h, rv_h = w.th.copy(), w.rv.copy()
+        rhod_h = w.rhod
+        q = sdm.Particles(w.cfg, th_h, rv_h, rhod_h, w.rhoCx, w.rhoCy, w.rhoCz, precision=args.precision)
+        th_pin = torch.from_numpy(th_h).pin_memory().numpy()
+        rv_pin = torch.from_numpy(rv_h).pin_memory().numpy()
+
+        def host_step():
+            if opts.get("cond", 1):
+                q.step_sync(opts, th_pin, rv_pin)
+            q.step_async(opts)
+            return q.wait()
+
+        for _ in range(args.warmup):
+            host_step()
+        dist_barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            host_step()
+        t_e2e = time.perf_counter() - t0
+        res["t_e2e"] = dist_max(t_e2e, world)
+        nbytes = w.th.size * 8
+        res["h2d"] = (2 * nbytes) if opts.get("cond", 1) else 0
+        res["d2h"] = (2 * nbytes if opts.get("cond", 1) else 0) + 128  # fields + the step's stats record
+        q.close()
+    p.close()
+    return res
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample(steps: int, warmup: int):
+    """The CPU oracle as it stands on a bounded sample of the workload: the
+    same 2D case restricted to 4 of the 75 columns (4 x 75 cells, 64 SD/cell,
+    19 200 SDs), full steps; single thread."""
+    import oracle
+    w = workloads.icmw_2d(nx=4)
+    o = oracle.Oracle(w.cfg)
+    o.init(w.th, w.rv, w.rhod)
+    for _ in range(warmup):
+        o.step_sync(w.opts)
+        o.step_async(w.opts, w.rhoCx, None, w.rhoCz)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step_sync(w.opts)
+        o.step_async(w.opts, w.rhoCx, None, w.rhoCz)
+    dt = time.perf_counter() - t0
+    return w.n_sd * steps / dt, w.n_sd, dt
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+
+    if args.impl == "reference":
+        if rank == 0:
+            v, n_sd, dt = oracle_sample(max(1, args.steps // 10), min(1, args.warmup))
+            w = make_workload(args.workload, 0)
+            line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                        warmup=args.warmup, ms_per_step=w.n_sd / v * 1e3, higher_is_better=True,
+                        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                        config=workload_desc(w),
+                        cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle",
+                                          sample=f"2D case, 4x75 cells x 64 SD ({n_sd} SDs), "
+                                                 f"{max(1, args.steps // 10)} full steps, {dt:.1f} s"),
+                        e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    res = run_gpu(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    w = res["w"]
+    total_sd_steps = res["n_sd"] * args.steps * world
+    value = total_sd_steps / res["t_dev"]
+    tim = res["timing"]
+    pk = peaks()
+    # dominant kernel: condensation, FP64-arithmetic bound
+    cond_ms = tim["cond_ms"] / max(1, tim["cond_launches"])
+    clk = res["clocks"]
+    sm_mhz = clk.get("sm_mhz") or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
+    fp64_peak = FP64_FLOPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    flops_per_sd_substep = float(os.environ.get("SDM_COND_FLOPS_PER_SD_SUBSTEP", "0") or 0)
+    roof = None
+    if flops_per_sd_substep > 0:
+        achieved = flops_per_sd_substep * res["n_sd"] * w.opts["sstp_cond"] / (cond_ms * 1e-3) / 1e12
+        roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
+                    frac=achieved / fp64_peak, traffic=None,
+                    peak_source="FP64 2 DFMA/SM/clk x 152 SMs at the sampled SM clock (derived)")
+    else:
+        # condensation bytes per SD-step over the kernel time, against HBM
+        bytes_per_launch = 40.0 * res["n_sd"]
+        achieved = bytes_per_launch / (cond_ms * 1e-3) / 1e9
+        hbm = pk.get("hbm_gbs", 6800.0)
+        roof = dict(kernel="k_condense", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
+                    frac=achieved / hbm, traffic=None,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6800")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=res["t_dev"] / args.steps * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64" if args.precision == "fp64" else "f64/f32",
+                data="synthetic", config=workload_desc(w), roofline=roof, clocks=clk,
+                gpu_launches=int(tim["launches"]),
+                phases_ms_per_step={k[:-3]: tim[k] / args.steps for k in tim if k.endswith("_ms")})
+    if "t_e2e" in res:
+        line["e2e"] = dict(value=total_sd_steps / res["t_e2e"], unit=UNIT, h2d_bytes_per_step=res["h2d"],
+                           d2h_bytes_per_step=res["d2h"])
+    if not args.no_cpu:
+        try:
+            v, n_sd, dt = oracle_sample(2, 1)
+            line["cpu_baseline"] = dict(value=v, unit=UNIT, cores=1, kind="oracle",
+                                        sample=f"2D case, 4x75 cells x 64 SD ({n_sd} SDs), 2 full steps "
+                                               f"after 1 warm-up, {dt:.1f} s, serial")
+        except Exception as e:  # the oracle is a baseline, never a fallback
+            line["cpu_baseline"] = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample=f"failed: {e}")
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

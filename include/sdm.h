@@ -1,0 +1,241 @@
+/*
+ * sdm.h - C ABI of the GB300 (sm_103a) super-droplet microphysics library.
+ *
+ * The library advances the particle-based ("super-droplet") warm-rain scheme
+ * of Arabas, Jaruga, Pawlowska & Grabowski, "libcloudph++ 0.2" (GMD 2015),
+ * Sec. 5, on one GPU.  The calls restate the paper's particles_t interface
+ * (Sec. 5.2.1, listings of opts_t, opts_init_t, arrinfo_t, particles_t and
+ * factory()) as plain C: init, step_sync, step_async, diagnostics.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an sdm_status; nothing is thrown across the ABI.
+ *    On failure sdm_last_error(ctx) holds a one-line message (a context-less
+ *    failure of sdm_init is reported by sdm_last_error(NULL)).
+ *  - Eulerian fields are caller-owned float64 arrays described by sdm_arr
+ *    (host or device memory).  Super-droplet state and the output buffer are
+ *    library-owned device memory.
+ *  - All GPU work of a context runs on the stream given to sdm_init, in
+ *    issue order.  Calls on one context must not be made concurrently from
+ *    several host threads.
+ *  - There is no CPU fallback: without a usable CUDA device sdm_init fails
+ *    with SDM_ECUDA.
+ */
+#ifndef SDM_H
+#define SDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDM_OK = 0,
+    SDM_EINVAL = 1,   /* invalid argument (message says which)                  */
+    SDM_ENOMEM = 2,   /* device or host allocation failed                       */
+    SDM_ECUDA = 3,    /* a CUDA runtime call failed                             */
+    SDM_ETIMEOUT = 4, /* sdm_wait deadline passed; the work is still in flight  */
+    SDM_ENUMERIC = 5, /* a kernel flagged a non-finite value                    */
+    SDM_ESTATE = 6,   /* call out of order (e.g. step_sync before sdm_wait)     */
+    SDM_ENOTSUP = 7   /* valid but not supported by this build (message says)   */
+} sdm_status;
+
+typedef struct sdm_ctx sdm_ctx;
+
+/* Description of a caller-owned n-dimensional float64 array, the paper's
+ * arrinfo_t (Sec. 5.2.1): data_zero points at element (0,...,0); element
+ * (i,j,k) is at data_zero + i*strides[0] + j*strides[1] + k*strides[2]
+ * (strides in elements, one per present dimension, in (x, y, z) order).
+ * data_zero == NULL means "argument absent" (arrinfo_t::is_null).
+ * on_device: 0 = host memory, 1 = device memory of the context's GPU. */
+typedef struct {
+    double *data_zero;
+    const int64_t *strides;
+    int on_device;
+} sdm_arr;
+
+/* One lognormal mode of the initial dry spectrum (Sec. 2.2 eq. lognormal,
+ * opts_init_t::dry_distros): mode radius [m], geometric standard deviation,
+ * concentration at STP [m^-3], hygroscopicity kappa. */
+typedef struct {
+    double rm, sigma, n_stp, kappa;
+} sdm_lognormal;
+
+enum { SDM_KERNEL_GEOMETRIC = 0, SDM_KERNEL_GOLOVIN = 1 };
+enum { SDM_INIT_LOGNORMAL = 0, SDM_INIT_EXPONENTIAL = 1 };
+enum { SDM_PRECISION_FP64 = 0, SDM_PRECISION_MIXED = 1 };
+enum { SDM_BACKEND_SERIAL = 0, SDM_BACKEND_OPENMP = 1, SDM_BACKEND_CUDA = 2 };
+
+/* Options fixed for the life of a simulation (opts_init_t, Sec. 5.2.1).
+ * nx, ny, nz: cells per dimension, 0 = dimension absent (all 0: parcel/box,
+ *   one cell); dx, dy, dz [m]; dt [s].
+ * sd_conc: super-droplets per cell per distinct kappa at initialisation
+ *   (sd_conc_mean); they are placed uniformly at random within each cell.
+ * kernel: SDM_KERNEL_GEOMETRIC (the paper's kernel_t::geometric, E = 1) or
+ *   SDM_KERNEL_GOLOVIN (K = golovin_b (V_i + V_j), for the box test).
+ * init_dist: SDM_INIT_LOGNORMAL uses modes[0..n_modes); SDM_INIT_EXPONENTIAL
+ *   draws wet volumes from an exponential law of mean exp_mean_volume [m^3]
+ *   with exp_n0 droplets per m^3 and no dry mass (box test).
+ * seed: key of the counter-based random numbers (runs are reproducible).
+ * physics: 0 bare Maxwell-Mason growth, 1 with the transition-regime and
+ *   ventilation corrections of Sec. 5.1.3.
+ * precision: SDM_PRECISION_FP64 or SDM_PRECISION_MIXED.
+ * backend: must be SDM_BACKEND_CUDA (factory(), Sec. 5.2.1; the other
+ *   back-ends return SDM_EINVAL). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, dt;
+    int sd_conc;
+    int kernel;
+    double golovin_b;
+    int init_dist;
+    double exp_mean_volume, exp_n0;
+    int n_modes;
+    const sdm_lognormal *modes;
+    uint64_t seed;
+    int physics;
+    int precision;
+    int backend;
+} sdm_opts_init;
+
+/* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10):
+ * process toggles, RH limit for drop growth, substep counts. */
+typedef struct {
+    int adve, sedi, cond, coal;
+    double RH_max;
+    int sstp_cond, sstp_coal;
+} sdm_opts;
+
+/* Counters accumulated since sdm_init (or the last sdm_stats_reset). */
+typedef struct {
+    uint64_t n_pairs;       /* candidate pairs examined                        */
+    uint64_t n_coll;        /* collision events                                */
+    uint64_t n_pgt1;        /* pairs with P_ij > 1 (no multiple coalescence)    */
+    uint64_t n_recycled;    /* zero-multiplicity super-droplets re-populated   */
+    uint64_t n_euler;       /* growth solves that took the Euler branch        */
+    uint64_t n_fallback;    /* growth solves finished by full bisection        */
+    uint64_t n_steps;       /* completed step_async calls                      */
+    uint64_t n_zero;        /* multiplicity-zero super-droplets now            */
+    double max_p;           /* largest P_ij seen                               */
+    double rainfall;        /* liquid mass through the bottom [kg]              */
+} sdm_stats;
+
+/* Per-phase device time [ms] accumulated while timing is on; measured with
+ * CUDA events on the context's stream around each group of launches. */
+typedef struct {
+    double cond_ms, recycle_ms, move_ms, sort_ms, coal_ms, diag_ms, copy_ms;
+    uint64_t cond_launches, coal_launches, launches;
+} sdm_timing;
+
+/* ---- life cycle --------------------------------------------------------- */
+
+/* factory() + particles_t::init (Sec. 5.2.1, 5.1.6): allocate the
+ * super-droplets on the device and initialise them from the dry spectrum
+ * (or the exponential box spectrum), at Koehler equilibrium with the cell
+ * humidity (RH = 0.95 where supersaturated).
+ * th, rv, rhod: theta [K], r_v [kg/kg], rho_d [kg/m^3] on cell centres,
+ *   shape (nx, ny, nz) without absent dimensions (one value for a box).
+ * rhoCx, rhoCy, rhoCz: rho_d times the Courant number on Arakawa-C edges,
+ *   shapes (nx+1, ny, nz), (nx, ny+1, nz), (nx, ny, nz+1); absent (NULL
+ *   data_zero) where the dimension is absent or the flow is zero.
+ * stream: cudaStream_t to use (NULL: the library creates one).
+ * out: receives the new context.  SDM_EINVAL on bad options, SDM_ENOMEM
+ *   if the state does not fit, SDM_ECUDA without a usable GPU. */
+sdm_status sdm_init(const sdm_opts_init *opts, sdm_arr th, sdm_arr rv, sdm_arr rhod,
+                    sdm_arr rhoCx, sdm_arr rhoCy, sdm_arr rhoCz, void *stream, sdm_ctx **out);
+
+/* Free all device memory of the context (waits for its stream first). */
+sdm_status sdm_destroy(sdm_ctx *ctx);
+
+/* Last error message of ctx (or of the last failed sdm_init for NULL). */
+const char *sdm_last_error(const sdm_ctx *ctx);
+
+/* ---- time stepping ------------------------------------------------------ */
+
+/* particles_t::step_sync (Sec. 5.1.3, 5.2.1): condensation/evaporation in
+ * sstp_cond substeps, each an implicit-in-r_w^2 growth solve per
+ * super-droplet followed by the per-cell update of r_v and theta, eq.
+ * (rhov_update).  th and rv are read and overwritten.  rhoCx/y/z, when
+ * present, replace the flow used by the next step_async; rhod, when present,
+ * replaces rho_d.  Host arrays are complete when the call returns; device
+ * arrays are complete in stream order.  SDM_ESTATE if a step_async has not
+ * been waited for. */
+sdm_status sdm_step_sync(sdm_ctx *ctx, const sdm_opts *opts, sdm_arr th, sdm_arr rv,
+                         sdm_arr rhoCx, sdm_arr rhoCy, sdm_arr rhoCz, sdm_arr rhod);
+
+/* particles_t::step_async (Sec. 5.1.2, 5.1.4, 5.1.5): recycling of
+ * zero-multiplicity super-droplets, advection, sedimentation, regrouping by
+ * cell and sstp_coal substeps of Monte-Carlo coalescence.  Enqueues the work
+ * and returns; sdm_wait completes it. */
+sdm_status sdm_step_async(sdm_ctx *ctx, const sdm_opts *opts);
+
+/* Wait at most timeout_s seconds (< 0: no limit) for the context's stream.
+ * rainfall_out (nullable) receives the accumulated rainfall [kg] (the paper's
+ * step_async return value).  SDM_ETIMEOUT leaves the work in flight. */
+sdm_status sdm_wait(sdm_ctx *ctx, double timeout_s, double *rainfall_out);
+
+/* ---- diagnostics (Sec. 5.2.1, diag_* and outbuf) ------------------------ */
+
+/* Select super-droplets with wet (wet=1) or dry (wet=0) radius in
+ * [r_min, r_max] for the following sdm_diag_mom calls. */
+sdm_status sdm_diag_rng(sdm_ctx *ctx, int wet, double r_min, double r_max);
+
+/* k-th moment (0 <= k <= 8) per cell, M = (rho_d dV)^-1 sum N r^k over the
+ * selected super-droplets, into the output buffer.  SDM_ESTATE before the
+ * first sdm_diag_rng. */
+sdm_status sdm_diag_mom(sdm_ctx *ctx, int k);
+
+/* Number of super-droplets with non-zero multiplicity per cell, into the
+ * output buffer. */
+sdm_status sdm_diag_sd_conc(sdm_ctx *ctx);
+
+/* Copy the output buffer (n_cells float64, row-major (x, y, z)) to dst,
+ * host (dst_on_device = 0, complete on return) or device memory. */
+sdm_status sdm_outbuf(sdm_ctx *ctx, double *dst, int dst_on_device);
+
+/* ---- state access (tests, checkpoint / resume) --------------------------- */
+
+enum {
+    SDM_ATTR_N = 0,     /* uint64 multiplicity               */
+    SDM_ATTR_RW2 = 1,   /* float64 wet radius squared [m^2]  */
+    SDM_ATTR_RD3 = 2,   /* float64 dry radius cubed [m^3]    */
+    SDM_ATTR_KAPPA = 3, /* float64 hygroscopicity            */
+    SDM_ATTR_X = 4,     /* float64 positions [m]             */
+    SDM_ATTR_Y = 5,
+    SDM_ATTR_Z = 6,
+    SDM_ATTR_UID = 7    /* uint32 super-droplet id           */
+};
+
+/* Number of super-droplets and cells of the context. */
+sdm_status sdm_sizes(const sdm_ctx *ctx, int64_t *n_sd, int64_t *n_cells);
+
+/* Copy one attribute of all n_sd super-droplets (storage order, the same for
+ * every attribute) to host memory dst (n elements, n == n_sd).  Completes
+ * before returning. */
+sdm_status sdm_get_attr(sdm_ctx *ctx, int attr, void *dst, int64_t n);
+
+/* Overwrite one attribute from host memory (storage order as returned by
+ * sdm_get_attr).  Positions changed this way regroup the super-droplets
+ * before the next step. */
+sdm_status sdm_set_attr(sdm_ctx *ctx, int attr, const void *src, int64_t n);
+
+/* Copy the library's current theta and r_v (n_cells each) to host memory. */
+sdm_status sdm_get_fields(sdm_ctx *ctx, double *th, double *rv);
+
+/* Step counter used in the random-number counters (completed step_async
+ * calls); set it to resume a checkpointed run bit-identically. */
+sdm_status sdm_get_step(const sdm_ctx *ctx, uint64_t *step);
+sdm_status sdm_set_step(sdm_ctx *ctx, uint64_t step);
+
+/* Counters (completes the stream first). */
+sdm_status sdm_get_stats(sdm_ctx *ctx, sdm_stats *out);
+
+/* Turn per-phase CUDA-event timing on (1) or off (0); read and reset it. */
+sdm_status sdm_timing_enable(sdm_ctx *ctx, int on);
+sdm_status sdm_get_timing(sdm_ctx *ctx, sdm_timing *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDM_H */

@@ -1,0 +1,442 @@
+// Regrouping gather + Monte-Carlo coalescence (paper Sec. 5.1.4).
+//
+// One launch per step handles every cell: it gathers the cell's
+// super-droplets through the counting-sort permutation, orders them by id
+// (so the stored layout, and with it every later floating-point sum, is
+// independent of atomic arrival order), runs the sstp_coal substeps on the
+// gathered copy and writes the cell contiguously into the other buffer.
+//
+// Per substep: the cell's n super-droplets with N > 0 are sorted by a
+// Philox key (ties by id) and paired (0,1), (2,3), ...; pair k collides when
+// its scaled probability, eq. (P_ij),
+//     P = max(N_i, N_j) K(r_i, r_j) dt''/dV * n (n-1) / (2 floor(n/2)),
+// exceeds the uniform number drawn for the pair's first member.
+//
+// Cells of up to 64 super-droplets: one warp each, two per lane, a
+// register bitonic sort through shuffles and per-warp shared memory for the
+// attributes.  Larger cells (up to kBigCellCap): one block each, bitonic
+// sort in shared memory, attributes in global memory.
+#include "sdm_internal.cuh"
+
+namespace sdm {
+
+struct CoalParams {
+    Grid g;
+    int sstp, coal, kernel;
+    double golovin_b;
+    uint64_t seed, step;
+};
+
+constexpr int kWarpCap = 64;
+constexpr int kWarpsPerBlock = 4;
+
+struct KeyRec {
+    unsigned long long key, pk;  // sort key, then (id << 32 | slot)
+};
+
+__device__ __forceinline__ bool rec_less(const KeyRec &a, const KeyRec &b) {
+    return a.key < b.key || (a.key == b.key && a.pk < b.pk);
+}
+
+__device__ __forceinline__ KeyRec shfl_rec(const KeyRec &r, int src) {
+    KeyRec o;
+    o.key = __shfl_sync(0xffffffffu, r.key, src);
+    o.pk = __shfl_sync(0xffffffffu, r.pk, src);
+    return o;
+}
+
+// bitonic sort of 64 records, lane l holding positions 2l (a) and 2l+1 (b)
+__device__ __forceinline__ void warp_sort64(KeyRec &a, KeyRec &b, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+        const bool up = ((2 * lane) & k) == 0;
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {
+                const bool sw = up ? rec_less(b, a) : rec_less(a, b);
+                if (sw) {
+                    const KeyRec t = a;
+                    a = b;
+                    b = t;
+                }
+            } else {
+                const int pl = lane ^ (j >> 1);
+                const KeyRec pa = shfl_rec(a, pl), pb = shfl_rec(b, pl);
+                const bool lower = (lane & (j >> 1)) == 0;
+                const bool keep_min = (up == lower);
+                const bool a_lt = rec_less(a, pa), b_lt = rec_less(b, pb);
+                if (keep_min) {
+                    if (!a_lt) a = pa;
+                    if (!b_lt) b = pb;
+                } else {
+                    if (a_lt) a = pa;
+                    if (b_lt) b = pb;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// collection kernel: geometric (E = 1) or Golovin
+__device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, double rw2b,
+                                           double vta, double vtb) {
+    if (p.kernel == SDM_KERNEL_GOLOVIN) {
+        const double Va = 4.0 / 3.0 * phys::pi * rw2a * sqrt(rw2a);
+        const double Vb = 4.0 / 3.0 * phys::pi * rw2b * sqrt(rw2b);
+        return p.golovin_b * (Va + Vb);
+    }
+    const double ra = sqrt(rw2a), rb = sqrt(rw2b);
+    const double dv = fabs(vta - vtb);
+    return phys::pi * (ra + rb) * (ra + rb) * dv;
+}
+
+// one collision event: the larger-N member (the first on a tie) keeps its
+// radii and loses the other's N; the other takes the merged droplet
+// (r_w^3, r_d^3 summed, kappa weighted by r_d^3).  Returns the merged slot.
+template <class Acc>
+__device__ __forceinline__ int collide(Acc &A, int a, int b) {
+    const int L = A.N(a) >= A.N(b) ? a : b;
+    const int S = L == a ? b : a;
+    A.setN(L, A.N(L) - A.N(S));
+    const double rwS = A.rw2(S), rwL = A.rw2(L);
+    const double r3 = rwS * sqrt(rwS) + rwL * sqrt(rwL);
+    const double r = cbrt(r3);
+    A.setrw2(S, r * r);
+    const double dS = A.rd3(S), dL = A.rd3(L);
+    const double m3 = dS + dL;
+    if (m3 > 0.0) A.setkappa(S, (A.kappa(S) * dS + A.kappa(L) * dL) / m3);
+    A.setrd3(S, m3);
+    return S;
+}
+
+// ---------------------------------------------------------------- warp path
+struct WarpSmem {
+    unsigned long long N[kWarpCap], acc[kWarpCap];
+    double rw2[kWarpCap], rd3[kWarpCap], kappa[kWarpCap], vt[kWarpCap];
+    uint32_t uid[kWarpCap];
+};
+
+struct SmemAcc {
+    WarpSmem *w;
+    __device__ unsigned long long N(int i) const { return w->N[i]; }
+    __device__ double rw2(int i) const { return w->rw2[i]; }
+    __device__ double rd3(int i) const { return w->rd3[i]; }
+    __device__ double kappa(int i) const { return w->kappa[i]; }
+    __device__ void setN(int i, unsigned long long v) { w->N[i] = v; }
+    __device__ void setrw2(int i, double v) { w->rw2[i] = v; }
+    __device__ void setrd3(int i, double v) { w->rd3[i] = v; }
+    __device__ void setkappa(int i, double v) { w->kappa[i] = v; }
+};
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_coal_warp(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
+                const double *amb, CoalParams p, uint32_t *bigcells, DevStats *st) {
+    __shared__ WarpSmem sm[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int c = blockIdx.x * kWarpsPerBlock + wib;
+    if (c >= p.g.n_cells) return;
+    WarpSmem &W = sm[wib];
+    const uint32_t beg = offset[c];
+    const int n = (int)(offset[c + 1] - beg);
+    if (n > kWarpCap) {
+        if (lane == 0) bigcells[atomicAdd(&st->n_big, 1u)] = (uint32_t)c;
+        return;
+    }
+    // gather and order by id
+    KeyRec r0{0, ~0ull}, r1{0, ~0ull};
+    if (2 * lane < n) {
+        const uint32_t pi = perm[beg + 2 * lane];
+        r0.pk = ((unsigned long long)src.uid[pi] << 32) | pi;
+    }
+    if (2 * lane + 1 < n) {
+        const uint32_t pi = perm[beg + 2 * lane + 1];
+        r1.pk = ((unsigned long long)src.uid[pi] << 32) | pi;
+    }
+    warp_sort64(r0, r1, lane);
+    const double nu = amb[2 * c], cX = amb[2 * c + 1];
+    const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = 2 * lane + r;
+        if (q < n) {
+            const uint32_t pi = (uint32_t)((r ? r1 : r0).pk & 0xffffffffu);
+            const uint32_t id = (uint32_t)((r ? r1 : r0).pk >> 32);
+            W.N[q] = src.N[pi];
+            W.rw2[q] = src.rw2[pi];
+            W.rd3[q] = src.rd3[pi];
+            W.kappa[q] = src.kappa[pi];
+            W.uid[q] = id;
+            W.vt[q] = geo ? vterm(W.rw2[q], nu, cX) : 0.0;
+            if (p.g.nx > 0) dst.x[beg + q] = src.x[pi];
+            if (p.g.ny > 0) dst.y[beg + q] = src.y[pi];
+            if (p.g.nz > 0) dst.z[beg + q] = src.z[pi];
+            dst.uid[beg + q] = id;
+        }
+    }
+    __syncwarp();
+    unsigned long long n_pairs = 0, n_coll = 0, n_pgt1 = 0;
+    double max_p = 0.0;
+    if (p.coal && n >= 2) {
+        SmemAcc A{&W};
+        const double dtpp = p.g.dt / p.sstp;
+        for (int sub = 0; sub < p.sstp; ++sub) {
+            KeyRec k0{~0ull, ~0ull}, k1{~0ull, ~0ull};
+            bool act0 = false, act1 = false;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int q = 2 * lane + r;
+                if (q < n && W.N[q] > 0) {
+                    const u64x4 w = philox4x64(W.uid[q], (uint64_t)sub, p.step, kStreamCoal, p.seed, 0);
+                    W.acc[q] = w.v[1];
+                    KeyRec kr{w.v[0], ((unsigned long long)W.uid[q] << 32) | (unsigned)q};
+                    if (r) {
+                        k1 = kr;
+                        act1 = true;
+                    } else {
+                        k0 = kr;
+                        act0 = true;
+                    }
+                }
+            }
+            const int m = __popc(__ballot_sync(0xffffffffu, act0)) + __popc(__ballot_sync(0xffffffffu, act1));
+            __syncwarp();
+            if (m < 2) continue;
+            warp_sort64(k0, k1, lane);
+            const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
+            if (2 * lane + 1 < m) {
+                const int a = (int)(k0.pk & 0xffu), b = (int)(k1.pk & 0xffu);
+                const double K = kernel_K(p, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b]);
+                const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
+                const double P = (double)Nmax * K * dtpp / p.g.dV * scale;
+                n_pairs++;
+                if (P > 1.0) n_pgt1++;
+                max_p = fmax(max_p, P);
+                if (u01(W.acc[a]) < P) {
+                    const int S = collide(A, a, b);
+                    if (geo) W.vt[S] = vterm(W.rw2[S], nu, cX);
+                    n_coll++;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    unsigned zeros = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = 2 * lane + r;
+        if (q < n) {
+            dst.N[beg + q] = W.N[q];
+            dst.rw2[beg + q] = W.rw2[q];
+            dst.rd3[beg + q] = W.rd3[q];
+            dst.kappa[beg + q] = W.kappa[q];
+            zeros += W.N[q] == 0;
+        }
+    }
+    zeros = __reduce_add_sync(0xffffffffu, zeros);
+    const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)n_pairs);
+    const unsigned nc = __reduce_add_sync(0xffffffffu, (unsigned)n_coll);
+    const unsigned ng = __reduce_add_sync(0xffffffffu, (unsigned)n_pgt1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) max_p = fmax(max_p, __shfl_xor_sync(0xffffffffu, max_p, o));
+    if (lane == 0) {
+        if (zeros) atomicAdd(&st->n_zero, (unsigned long long)zeros);
+        if (np) atomicAdd(&st->n_pairs, (unsigned long long)np);
+        if (nc) atomicAdd(&st->n_coll, (unsigned long long)nc);
+        if (ng) atomicAdd(&st->n_pgt1, (unsigned long long)ng);
+        if (max_p > 0.0) atomic_max_pos(&st->max_p_bits, max_p);
+    }
+}
+
+// ---------------------------------------------------------------- block path
+struct GlobalAcc {
+    SdArrays s;
+    uint32_t beg;
+    __device__ unsigned long long N(int i) const { return s.N[beg + i]; }
+    __device__ double rw2(int i) const { return s.rw2[beg + i]; }
+    __device__ double rd3(int i) const { return s.rd3[beg + i]; }
+    __device__ double kappa(int i) const { return s.kappa[beg + i]; }
+    __device__ void setN(int i, unsigned long long v) { s.N[beg + i] = v; }
+    __device__ void setrw2(int i, double v) { s.rw2[beg + i] = v; }
+    __device__ void setrd3(int i, double v) { s.rd3[beg + i] = v; }
+    __device__ void setkappa(int i, double v) { s.kappa[beg + i] = v; }
+};
+
+constexpr int kBigBlock = 1024;
+
+__device__ void block_sort(unsigned long long *key, unsigned long long *pk, int npow2) {
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long ka = key[i], kb = key[ixj], pa = pk[i], pb = pk[ixj];
+                    const bool a_gt = ka > kb || (ka == kb && pa > pb);
+                    if (a_gt == up) {
+                        key[i] = kb;
+                        key[ixj] = ka;
+                        pk[i] = pb;
+                        pk[ixj] = pa;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBigBlock)
+    k_coal_block(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
+                 const double *amb, CoalParams p, const uint32_t *bigcells, DevStats *st) {
+    extern __shared__ unsigned long long smem[];
+    unsigned long long *skey = smem, *spk = smem + kBigCellCap, *sacc = smem + 2 * kBigCellCap;
+    __shared__ int s_m;
+    __shared__ unsigned long long s_cnt[4];
+    __shared__ unsigned long long s_maxp;
+    const unsigned nbig = st->n_big;
+    for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const int c = (int)bigcells[bi];
+        const uint32_t beg = offset[c];
+        const int n = (int)(offset[c + 1] - beg);
+        if (n > kBigCellCap) {
+            if (threadIdx.x == 0) atomicOr(&st->flags, kFlagBigCell);
+            continue;
+        }
+        int npow2 = 1;
+        while (npow2 < n) npow2 <<= 1;
+        for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
+            skey[t] = 0;
+            if (t < n) {
+                const uint32_t pi = perm[beg + t];
+                spk[t] = ((unsigned long long)src.uid[pi] << 32) | pi;
+            } else {
+                spk[t] = ~0ull;
+            }
+        }
+        __syncthreads();
+        block_sort(skey, spk, npow2);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const uint32_t pi = (uint32_t)(spk[t] & 0xffffffffu);
+            const uint32_t o = beg + t;
+            dst.N[o] = src.N[pi];
+            dst.rw2[o] = src.rw2[pi];
+            dst.rd3[o] = src.rd3[pi];
+            dst.kappa[o] = src.kappa[pi];
+            if (p.g.nx > 0) dst.x[o] = src.x[pi];
+            if (p.g.ny > 0) dst.y[o] = src.y[pi];
+            if (p.g.nz > 0) dst.z[o] = src.z[pi];
+            dst.uid[o] = (uint32_t)(spk[t] >> 32);
+        }
+        if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_maxp = 0;
+        __syncthreads();
+        const double nu = amb[2 * c], cX = amb[2 * c + 1];
+        const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
+        GlobalAcc A{dst, beg};
+        if (p.coal && n >= 2) {
+            const double dtpp = p.g.dt / p.sstp;
+            for (int sub = 0; sub < p.sstp; ++sub) {
+                if (threadIdx.x == 0) s_m = 0;
+                __syncthreads();
+                int my_m = 0;
+                for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
+                    if (t < n && dst.N[beg + t] > 0) {
+                        const uint32_t id = dst.uid[beg + t];
+                        const u64x4 w = philox4x64(id, (uint64_t)sub, p.step, kStreamCoal, p.seed, 0);
+                        skey[t] = w.v[0];
+                        sacc[t] = w.v[1];
+                        spk[t] = ((unsigned long long)id << 32) | (unsigned)t;
+                        my_m++;
+                    } else {
+                        skey[t] = ~0ull;
+                        spk[t] = ~0ull;
+                    }
+                }
+                atomicAdd(&s_m, my_m);
+                __syncthreads();
+                const int m = s_m;
+                if (m < 2) {
+                    __syncthreads();
+                    continue;
+                }
+                block_sort(skey, spk, npow2);
+                const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
+                unsigned long long np = 0, nc = 0, ng = 0;
+                double mp = 0.0;
+                for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+                    const int a = (int)(spk[2 * k] & 0xffffffffu), b = (int)(spk[2 * k + 1] & 0xffffffffu);
+                    const double rwa = A.rw2(a), rwb = A.rw2(b);
+                    const double K = kernel_K(p, rwa, rwb, geo ? vterm(rwa, nu, cX) : 0.0,
+                                              geo ? vterm(rwb, nu, cX) : 0.0);
+                    const unsigned long long Na = A.N(a), Nb = A.N(b);
+                    const unsigned long long Nmax = Na > Nb ? Na : Nb;
+                    const double P = (double)Nmax * K * dtpp / p.g.dV * scale;
+                    np++;
+                    if (P > 1.0) ng++;
+                    mp = fmax(mp, P);
+                    if (u01(sacc[a]) < P) {
+                        collide(A, a, b);
+                        nc++;
+                    }
+                }
+                if (np) atomicAdd(&s_cnt[0], np);
+                if (nc) atomicAdd(&s_cnt[1], nc);
+                if (ng) atomicAdd(&s_cnt[2], ng);
+                if (mp > 0.0) atomicMax(&s_maxp, (unsigned long long)__double_as_longlong(mp));
+                __syncthreads();
+            }
+        }
+        unsigned z = 0;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) z += dst.N[beg + t] == 0;
+        if (z) atomicAdd(&s_cnt[3], (unsigned long long)z);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cnt[0]) atomicAdd(&st->n_pairs, s_cnt[0]);
+            if (s_cnt[1]) atomicAdd(&st->n_coll, s_cnt[1]);
+            if (s_cnt[2]) atomicAdd(&st->n_pgt1, s_cnt[2]);
+            if (s_cnt[3]) atomicAdd(&st->n_zero, s_cnt[3]);
+            if (s_maxp) atomicMax(&st->max_p_bits, s_maxp);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
+    CoalParams p;
+    p.g = c->grid;
+    p.sstp = o.sstp_coal;
+    p.coal = coal ? 1 : 0;
+    p.kernel = c->oi.kernel;
+    p.golovin_b = c->oi.golovin_b;
+    p.seed = c->oi.seed;
+    p.step = c->step;
+    SdArrays src = c->buf[c->cur], dst = c->buf[c->cur ^ 1];
+    cudaError_t e = cudaMemsetAsync(&c->dstats->n_big, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->dstats->n_zero, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    const int nb = (c->grid.n_cells + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_coal_warp<<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
+                                                           c->bigcells, c->dstats);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(unsigned long long) * 3 * kBigCellCap;
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_coal_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    int blocks = nsm > 0 ? nsm : 152;
+    if (blocks > c->grid.n_cells) blocks = c->grid.n_cells;
+    k_coal_block<<<blocks, kBigBlock, smem, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
+                                                         c->bigcells, c->dstats);
+    return cudaGetLastError();
+}
+
+}  // namespace sdm

@@ -1,0 +1,266 @@
+// Internal declarations of the super-droplet library (sm_103a).
+//
+// Device physics restates the paper (Arabas et al., libcloudph++ 0.2):
+// Sec. 5.1.3 (phase changes), 5.1.4 (coalescence), 5.1.5 (sedimentation),
+// 5.1.6 (initialisation), Appendix A (T, p from theta, r_v, rho_d) and the
+// list of symbols.  Where the paper is silent the library takes the same
+// readings as its test oracle (listed in the project's design notes).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sdm.h"
+
+namespace sdm {
+
+// ---------------------------------------------------------------- constants
+// list of symbols: rho_w, sigma_w, c_pd, c_pv, c_l, l_v0; the rest are the
+// library's readings of values the paper does not print
+namespace phys {
+constexpr double pi = 3.14159265358979323846;
+constexpr double rho_w = 1000.0, sigma_w = 0.072;
+constexpr double c_pd = 1005.0, c_pv = 1850.0, c_l = 4218.0, l_v0 = 2.5e6;
+constexpr double R_d = 287.0, R_v = 461.5;
+constexpr double T0 = 273.16, p_vs0 = 611.73, grav = 9.81, p1000 = 1.0e5;
+constexpr double D0 = 2.26e-5, K0 = 2.4e-2;
+constexpr double delta0 = 9.06, C0 = 0.292;
+constexpr double rho_stp = 101325.0 / (R_d * 293.15);
+}  // namespace phys
+
+constexpr int kMaxModes = 8;
+constexpr int kBigCellCap = 8192;  // largest cell handled by the block path
+
+// ---------------------------------------------------------------- RNG
+// Philox4x64-10 (Salmon et al., SC'11): counter (id, substep, step, stream)
+// under key (seed, 0); streams: 1 coalescence, 3 initialisation.
+enum { kStreamCoal = 1, kStreamInit = 3 };
+
+struct u64x4 {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ u64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                            uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t h0 = __umul64hi(M0, c0), l0 = M0 * c0;
+        const uint64_t h1 = __umul64hi(M1, c2), l1 = M1 * c2;
+        const uint64_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = l1;
+        c2 = n2;
+        c3 = l0;
+    }
+    u64x4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+// open-interval (0,1) uniform: 52 random bits plus one half, times 2^-52
+__device__ __forceinline__ double u01(uint64_t v) {
+    return ((double)(v >> 12) + 0.5) * 0x1p-52;
+}
+
+// ---------------------------------------------------------------- thermo
+struct Thermo {
+    double th, rv, rhod;
+    double T, lv, rho_v, rho_vs, rho_v_eff, dth_drv, A, Dterm;
+    double rho_a, nu, lambda_D, lambda_K, Sc, Pr, cX;
+};
+
+// Appendix A: T and p from theta, r_v, rho_d; Sec. 5.1.3 quantities.
+__device__ __forceinline__ Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
+    using namespace phys;
+    Thermo t;
+    t.th = th;
+    t.rv = rv;
+    t.rhod = rhod;
+    t.T = pow(th * pow(rhod * R_d / p1000, R_d / c_pd), c_pd / (c_pd - R_d));
+    t.lv = l_v0 + (c_pv - c_l) * (t.T - T0);
+    // Clausius-Clapeyron integrated with the linear l_v(T)
+    const double lnp = (l_v0 + (c_l - c_pv) * T0) / R_v * (1.0 / T0 - 1.0 / t.T) -
+                       (c_l - c_pv) / R_v * log(t.T / T0);
+    t.rho_vs = p_vs0 * exp(lnp) / (R_v * t.T);
+    t.rho_v = rv * rhod;
+    t.rho_v_eff = fmin(t.rho_v, RH_max * t.rho_vs);
+    t.dth_drv = -th * t.lv / (c_pd * t.T);
+    t.A = 2.0 * sigma_w / (R_v * t.T * rho_w);
+    t.Dterm = t.rho_vs * t.lv / t.T * (t.lv / (R_v * t.T) - 1.0);
+    t.rho_a = rhod * (1.0 + rv);
+    const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * pow(t.T / 273.0, 1.5);
+    t.nu = mu / t.rho_a;
+    t.lambda_D = 2.0 * D0 / sqrt(8.0 * R_v * t.T / pi);
+    t.lambda_K = 2.0 * K0 / (t.rho_a * c_pd * sqrt(8.0 * R_d * t.T / pi));
+    t.Sc = t.nu / D0;
+    t.Pr = t.nu * t.rho_a * c_pd / K0;
+    t.cX = 32.0 / 3.0 * (rho_w - t.rho_a) / t.rho_a * grav / (t.nu * t.nu);
+    return t;
+}
+
+// Khvorostyanov & Curry (2002) sphere: Re(X), X = cX r^3 (Best number)
+__device__ __forceinline__ double reynolds(double rw2, double cX) {
+    using namespace phys;
+    const double r = sqrt(rw2);
+    if (!(r > 0.0)) return 0.0;
+    const double X = cX * rw2 * r;
+    const double c1 = 4.0 / (delta0 * delta0 * sqrt(C0));
+    const double e = c1 * sqrt(X);
+    const double s = e / (sqrt(1.0 + e) + 1.0);
+    return delta0 * delta0 / 4.0 * s * s;
+}
+
+// terminal velocity v_t = Re nu / (2 r)
+__device__ __forceinline__ double vterm(double rw2, double nu, double cX) {
+    const double r = sqrt(rw2);
+    if (!(r > 0.0)) return 0.0;
+    return reynolds(rw2, cX) * nu / (2.0 * r);
+}
+
+__device__ __forceinline__ double fuchs_sutugin(double Kn) {
+    return (1.0 + Kn) / (1.0 + (4.0 / 3.0 + 0.377) * Kn + 4.0 / 3.0 * Kn * Kn);
+}
+
+// dr_w^2/dt = 2 D_eff / rho_w (rho_v - rho_o), eq. (maxmason), (rho_circ)
+__device__ __forceinline__ double growth(double x, double rd3, double kappa, const Thermo &t,
+                                         int physics) {
+    using namespace phys;
+    const double r = sqrt(x);
+    const double r3 = x * r;
+    const double aw = (r3 - rd3) / (r3 - rd3 * (1.0 - kappa));
+    const double rho_o = t.rho_vs * aw * exp(t.A / r);
+    double D = D0, K = K0;
+    if (physics) {
+        const double bM = fuchs_sutugin(t.lambda_D / r);
+        const double bT = fuchs_sutugin(t.lambda_K / r);
+        const double Re = reynolds(x, t.cX);
+        const double fRe = Re > 1.0 ? pow(Re, 0.077) : 1.0;
+        const double Sh = 1.0 + cbrt(1.0 + Re * t.Sc) * fRe;
+        const double Nu = 1.0 + cbrt(1.0 + Re * t.Pr) * fRe;
+        D = D0 * bM * Sh / 2.0;
+        K = K0 * bT * Nu / 2.0;
+    }
+    const double Deff = 1.0 / (1.0 / D + t.Dterm / K);
+    return 2.0 * Deff / rho_w * (t.rho_v_eff - rho_o);
+}
+
+__device__ __forceinline__ double rd2_of(double rd3) {
+    const double rd = cbrt(rd3);
+    return rd * rd;
+}
+
+// ---------------------------------------------------------------- context
+struct DevStats {
+    unsigned long long n_pairs, n_coll, n_pgt1, n_recycled, n_euler, n_fallback, n_zero;
+    unsigned long long max_p_bits;  // max of non-negative doubles via uint order
+    double rainfall;
+    unsigned int flags;  // kFlag* bits
+    unsigned int n_big;  // cells routed to the block coalescence path
+    unsigned int n_rc_zero, n_rc_donor;
+};
+enum : unsigned { kFlagNumeric = 1u, kFlagBigCell = 2u };
+
+struct Grid {
+    int nx, ny, nz;     // 0 = absent
+    int NX, NY, NZ;     // max(n, 1)
+    double dx, dy, dz;  // cell sizes
+    double dt, dV;
+    int n_cells;
+};
+
+struct SdArrays {  // one buffer of the structure-of-arrays state
+    unsigned long long *N;
+    double *rw2, *rd3, *kappa, *x, *y, *z;
+    uint32_t *uid;
+};
+
+struct PhaseTimer {
+    cudaEvent_t a, b;
+    int phase;
+};
+
+}  // namespace sdm
+
+struct sdm_ctx {
+    sdm_opts_init oi;
+    std::vector<sdm_lognormal> modes;
+    int G = 1;
+    std::vector<double> gkappa, lnr_min, lnr_max;
+    sdm::Grid grid;
+    int64_t n_sd = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    sdm::SdArrays buf[2];
+    int cur = 0;
+    uint32_t *newcell = nullptr, *slot = nullptr, *perm = nullptr;
+    uint32_t *count = nullptr, *offset = nullptr, *bigcells = nullptr;
+    double *th = nullptr, *rv = nullptr, *rhod = nullptr, *amb = nullptr, *outbuf = nullptr;
+    double *rhoC[3] = {nullptr, nullptr, nullptr};
+    uint32_t *scan_tmp = nullptr;
+    void *rc_tmp = nullptr;
+    size_t rc_tmp_bytes = 0;
+    sdm::DevStats *dstats = nullptr;
+    sdm::DevStats *hstats = nullptr;  // pinned landing area of stats copies
+    sdm::DevStats mirror{};           // last copy pulled from the device
+    uint64_t host_recycled = 0;       // super-droplets re-populated so far
+    cudaEvent_t done_event = nullptr; // end of the last step_async
+
+    bool async_in_flight = false;
+    bool layout_dirty = false;
+    bool rng_set = false;
+    int diag_wet = 1;
+    double diag_rmin = 0.0, diag_rmax = 0.0;
+    uint64_t step = 0;
+    uint64_t known_zeros = 0;
+    std::string err;
+
+    bool timing = false;
+    std::vector<sdm::PhaseTimer> timers;
+    std::vector<cudaEvent_t> event_pool;
+    sdm_timing tacc{};
+};
+
+namespace sdm {
+
+// launch wrappers (each returns the first CUDA error of its launches)
+cudaError_t launch_init(sdm_ctx *c);
+cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o);
+cudaError_t launch_ambient(sdm_ctx *c);
+cudaError_t launch_move(sdm_ctx *c, const sdm_opts &o);
+cudaError_t launch_regroup(sdm_ctx *c);  // scan + perm (after move)
+cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal);
+cudaError_t launch_recycle_compact(sdm_ctx *c);
+cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
+cudaError_t launch_moments(sdm_ctx *c, int k);
+cudaError_t launch_sd_conc(sdm_ctx *c);
+cudaError_t launch_field_gather(double *dst, const double *src, const int64_t *strides, int ndim,
+                                const int *shape, cudaStream_t s);
+cudaError_t launch_field_scatter(double *dst, const double *src, const int64_t *strides,
+                                 int ndim, const int *shape, cudaStream_t s);
+
+// sort of (key_hi, key_lo, payload) records ascending by (key_hi, key_lo)
+struct SortRec {
+    unsigned long long hi;
+    uint32_t lo, val;
+};
+cudaError_t sort_records(SortRec *rec, uint32_t n, uint32_t n_pow2, cudaStream_t s);
+
+inline unsigned grid_for(int64_t n, int block) {
+    return (unsigned)((n + block - 1) / block);
+}
+
+}  // namespace sdm

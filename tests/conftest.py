@@ -18,3 +18,16 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+def _has_gpu() -> bool:
+    return os.path.exists("/dev/nvidiactl") or os.path.exists("/dev/nvidia0")
+
+
+def pytest_collection_modifyitems(config, items):
+    if _has_gpu():
+        return
+    skip = pytest.mark.skip(reason="no CUDA device on this machine")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)

@@ -1,0 +1,208 @@
+"""Parity of the CUDA library (through its C ABI) with the CPU oracle on the
+same seeded inputs: element by element, multiplicities bit-exact, radii,
+mixing ratios and moments within 1e-12 relative (FP64)."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import (RTOL, assert_close, compare_states, gpu_particles, oracle_sim, oracle_state,
+                         present_dims)
+from paper_1310_1905_gb300 import sdm
+
+pytestmark = pytest.mark.gpu
+
+COND_ONLY = dict(adve=0, sedi=0, cond=1, coal=0, sstp_cond=10, sstp_coal=10)
+COAL_ONLY = dict(adve=0, sedi=0, cond=0, coal=1, sstp_cond=10, sstp_coal=10)
+MOVE_ONLY = dict(adve=1, sedi=1, cond=0, coal=0, sstp_cond=10, sstp_coal=10)
+ALL = dict(adve=1, sedi=1, cond=1, coal=1, sstp_cond=10, sstp_coal=10)
+
+
+def small_2d(seed=0, nx=9, nz=13, sd=20):
+    # several warps' worth of cells, a ragged count per cell, supersaturated top
+    return workloads.icmw_2d(nx=nx, nz=nz, sd_conc=sd, seed=seed, dz=115.0)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_init_matches_oracle(seed):
+    w = small_2d(seed)
+    p = gpu_particles(w)
+    o = oracle_sim(w)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+
+
+def test_init_golovin_box():
+    w = workloads.golovin_box(seed=5)
+    p = gpu_particles(w)
+    o = oracle_sim(w)
+    compare_states(p.state(), oracle_state(o, ()))
+
+
+def test_condensation_matches_oracle():
+    w = small_2d(3)
+    p, o = gpu_particles(w), oracle_sim(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(4):
+        p.step_sync(COND_ONLY, th, rv)
+        o.step_sync(COND_ONLY)
+        assert_close("theta", th.ravel(), o.th)
+        assert_close("r_v", rv.ravel(), o.rv)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    assert np.abs(o.rv - w.rv.ravel()).max() > 1e-6  # something condensed
+
+
+def test_condensation_bare_maxwell_mason():
+    w = workloads.icmw_2d(nx=5, nz=11, sd_conc=12, seed=4, dz=130.0, physics=0)
+    p, o = gpu_particles(w), oracle_sim(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(3):
+        p.step_sync(COND_ONLY, th, rv)
+        o.step_sync(COND_ONLY)
+    assert_close("theta", th.ravel(), o.th)
+    assert_close("r_v", rv.ravel(), o.rv)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+
+
+def test_transport_matches_oracle():
+    w = small_2d(5)
+    p, o = gpu_particles(w), oracle_sim(w)
+    for _ in range(6):
+        p.step_async(MOVE_ONLY)
+        rain_g = p.wait()
+        o.step_async(MOVE_ONLY, w.rhoCx, None, w.rhoCz)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    assert rain_g == pytest.approx(o.stats.rainfall, rel=1e-12, abs=0.0)
+
+
+def test_coalescence_golovin_box_full_run():
+    """Config: Golovin box, 8192 super-droplets, 1 s steps, 3600 s."""
+    w = workloads.golovin_box(seed=2)
+    p, o = gpu_particles(w), oracle_sim(w)
+    for t in range(1, 3601):
+        p.step_async(w.opts)
+        p.wait()
+        o.step_async(w.opts)
+        if t in (1, 10, 100, 1200, 3600):
+            compare_states(p.state(), oracle_state(o, ()))
+    st = p.stats()
+    assert st["n_coll"] == o.stats.n_coll
+    assert st["n_recycled"] == o.stats.n_recycled
+    assert st["n_pgt1"] == o.stats.n_pgt1
+
+
+def test_coalescence_geometric_2d():
+    w = small_2d(6, sd=40)
+    p, o = gpu_particles(w), oracle_sim(w)
+    # grow big drops first so that collisions happen: condense for a while
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(3):
+        p.step_sync(COND_ONLY, th, rv)
+        o.step_sync(COND_ONLY)
+    for _ in range(5):
+        p.step_async(COAL_ONLY)
+        p.wait()
+        o.step_async(COAL_ONLY)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    assert p.stats()["n_pairs"] == o.stats.n_pairs
+
+
+def test_full_steps_2d():
+    w = small_2d(7)
+    p, o = gpu_particles(w), oracle_sim(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(8):
+        p.step_sync(ALL, th, rv)
+        p.step_async(ALL)
+        p.wait()
+        o.step_sync(ALL)
+        o.step_async(ALL, w.rhoCx, None, w.rhoCz)
+    assert_close("theta", th.ravel(), o.th)
+    assert_close("r_v", rv.ravel(), o.rv)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    st = p.stats()
+    assert st["n_coll"] == o.stats.n_coll and st["n_pairs"] == o.stats.n_pairs
+
+
+def test_full_steps_3d_small():
+    w = workloads.updraft_3d(nx=4, ny=3, nz=9, sd_conc=10, seed=8, dx=150.0)
+    p, o = gpu_particles(w), oracle_sim(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(6):
+        p.step_sync(ALL, th, rv)
+        p.step_async(ALL)
+        p.wait()
+        o.step_sync(ALL)
+        o.step_async(ALL, w.rhoCx.ravel(), w.rhoCy.ravel(), w.rhoCz.ravel())
+    assert_close("theta", th.ravel(), o.th)
+    assert_close("r_v", rv.ravel(), o.rv)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+
+
+def test_recycling_matches_oracle():
+    w = small_2d(9)
+    p, o = gpu_particles(w), oracle_sim(w)
+    # zero out a pseudo-random fifth of the multiplicities on both sides
+    g = p.state()
+    rng = np.random.default_rng(0)
+    zero_ids = set(rng.choice(len(g["uid"]), size=len(g["uid"]) // 5, replace=False).tolist())
+    uid_store = p.attr("uid")
+    N_store = p.attr("N")
+    N_store[[i for i, u in enumerate(uid_store) if int(u) in zero_ids]] = 0
+    sdm.sdm_set_attr(p.ctx, "N", N_store)
+    o.state.N[[i for i, u in enumerate(o.state.uid) if int(u) in zero_ids]] = 0
+    opts = dict(COAL_ONLY, coal=0)
+    p.step_async(opts)
+    p.wait()  # first wait learns about the zeros
+    o.step_async(opts)
+    p.step_async(opts)
+    p.wait()
+    o.step_async(opts)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    assert p.stats()["n_recycled"] == o.stats.n_recycled > 0
+
+
+def test_diagnostics_match_oracle():
+    w = small_2d(10)
+    p, o = gpu_particles(w), oracle_sim(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    p.step_sync(COND_ONLY, th, rv)
+    o.step_sync(COND_ONLY)
+    for wet, rmin, rmax in ((True, 0.0, 1.0), (True, 0.5e-6, 25e-6), (False, 1e-8, 1e-6)):
+        for k in range(4):
+            assert_close(f"M{k}", p.diag_moments(wet, rmin, rmax, k), o.moments(wet, rmin, rmax, k),
+                         atol=1e-300)
+    assert np.array_equal(p.diag_sd_conc(), o.sd_conc())
+
+
+def test_device_resident_fields_and_strides():
+    torch = pytest.importorskip("torch")
+    w = small_2d(11)
+    p, o = gpu_particles(w), oracle_sim(w)
+    # fields on the device, transposed storage (strides (1, nx))
+    th = torch.tensor(w.th.T.copy(), dtype=torch.float64, device="cuda").t()
+    rv = torch.tensor(w.rv.T.copy(), dtype=torch.float64, device="cuda").t()
+    assert th.stride() == (1, w.th.shape[0])
+    p.step_sync(COND_ONLY, th, rv)
+    o.step_sync(COND_ONLY)
+    torch.cuda.synchronize()
+    assert_close("theta", th.cpu().numpy().ravel(), o.th)
+    assert_close("r_v", rv.cpu().numpy().ravel(), o.rv)
+
+
+def test_status_codes():
+    w = small_2d(12)
+    p = gpu_particles(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    p.step_async(ALL)
+    with pytest.raises(sdm.SdmError) as e:
+        p.step_sync(ALL, th, rv)          # step_sync before wait
+    assert e.value.status == 6
+    p.wait()
+    with pytest.raises(sdm.SdmError) as e:
+        sdm.sdm_diag_mom(p.ctx, 2)        # diag_mom before diag_rng
+    assert e.value.status == 6
+    with pytest.raises(sdm.SdmError) as e:
+        sdm.sdm_init(w.cfg, w.th, w.rv, w.rhod, backend="openmp")
+    assert e.value.status == 1
+    bad = dict(w.cfg, sd_conc=0)
+    with pytest.raises(sdm.SdmError):
+        sdm.sdm_init(bad, w.th, w.rv, w.rhod)
