@@ -66,6 +66,7 @@ enum { SDM_KERNEL_GEOMETRIC = 0, SDM_KERNEL_GOLOVIN = 1 };
 enum { SDM_INIT_LOGNORMAL = 0, SDM_INIT_EXPONENTIAL = 1 };
 enum { SDM_PRECISION_FP64 = 0, SDM_PRECISION_MIXED = 1 };
 enum { SDM_BACKEND_SERIAL = 0, SDM_BACKEND_OPENMP = 1, SDM_BACKEND_CUDA = 2 };
+enum { SDM_SOLVER_BISECT = 0, SDM_SOLVER_FAST = 1 };
 
 /* Options fixed for the life of a simulation (opts_init_t, Sec. 5.2.1).
  * nx, ny, nz: cells per dimension, 0 = dimension absent (all 0: parcel/box,
@@ -82,7 +83,12 @@ enum { SDM_BACKEND_SERIAL = 0, SDM_BACKEND_OPENMP = 1, SDM_BACKEND_CUDA = 2 };
  *   ventilation corrections of Sec. 5.1.3.
  * precision: SDM_PRECISION_FP64 or SDM_PRECISION_MIXED.
  * backend: must be SDM_BACKEND_CUDA (factory(), Sec. 5.2.1; the other
- *   back-ends return SDM_EINVAL). */
+ *   back-ends return SDM_EINVAL).
+ * cond_solver: SDM_SOLVER_BISECT runs the paper's bisection (Sec. 5.1.3) in
+ *   FP64 throughout; SDM_SOLVER_FAST (the default in the bindings) takes the
+ *   same bracket, the same midpoints and the same sign decisions, decided in
+ *   FP32 where an error bound proves the sign, then finishes with a
+ *   bracketed FP64 Newton/secant iteration to the same sign change. */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz, dt;
@@ -97,6 +103,7 @@ typedef struct {
     int physics;
     int precision;
     int backend;
+    int cond_solver;
 } sdm_opts_init;
 
 /* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10):
@@ -227,6 +234,21 @@ sdm_status sdm_get_fields(sdm_ctx *ctx, double *th, double *rv);
  * calls); set it to resume a checkpointed run bit-identically. */
 sdm_status sdm_get_step(const sdm_ctx *ctx, uint64_t *step);
 sdm_status sdm_set_step(sdm_ctx *ctx, uint64_t step);
+
+/* ---- regrouping of caller-held particles -------------------------------- */
+
+/* Counting sort of particles by grid cell, the regrouping that the cell-wise
+ * pairing (Sec. 5.1.4) and cell sums (Sec. 5.1.3, eq. rhov_update) rest on.
+ * cell: n cell indices in [0, n_cells) (device memory, uint32).
+ * perm: out, n particle indices grouped by cell (device); the order within
+ *   a cell is unspecified.  offsets: out, n_cells + 1 entries (device):
+ *   cell c holds perm[offsets[c] .. offsets[c+1]).
+ * Work runs on stream (cudaStream_t, NULL = legacy default stream); scratch
+ * is allocated and freed on that stream; the call completes before it
+ * returns.  SDM_EINVAL if a cell index is out of range (nothing is written
+ * for it) or an argument is invalid, SDM_ENOMEM if scratch is unavailable. */
+sdm_status sdm_cell_sort(const uint32_t *cell, int64_t n, int32_t n_cells, uint32_t *perm,
+                         uint32_t *offsets, void *stream);
 
 /* Counters (completes the stream first). */
 sdm_status sdm_get_stats(sdm_ctx *ctx, sdm_stats *out);

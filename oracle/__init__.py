@@ -110,6 +110,9 @@ def lib():
             L.orc_rd_range.argtypes = [_P(Domain), C.c_int, _P(_D), _P(_D)]; L.orc_rd_range.restype = C.c_int
             L.orc_init_cells.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), C.c_int64, _P(C.c_int64), _P(SDs)]
             L.orc_init_cells.restype = C.c_int
+            L.orc_init_cells_nreal.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), C.c_int64, _P(C.c_int64),
+                                               _P(SDs), _P(_D)]
+            L.orc_init_cells_nreal.restype = C.c_int
             L.orc_condense.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), _P(Stats)]
             L.orc_recycle.argtypes = [_P(SDs), _P(Stats)]
             L.orc_advect.argtypes = [_P(Domain), _P(SDs), _P(_D), _P(_D), _P(_D), _P(_D)]
@@ -246,22 +249,26 @@ class Oracle:
             raise RuntimeError(f"orc_rd_range failed ({rc})")
         return lo.value, hi.value
 
-    def init_cells(self, th, rv, rhod, cells) -> State:
+    def init_cells(self, th, rv, rhod, cells, with_nreal=False):
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         n = len(cells) * self.n_groups * self.dom.sd_conc
         st = State(n)
         s = st.struct()
-        rc = lib().orc_init_cells(C.byref(self.dom), _dp(th), _dp(rv), _dp(rhod), len(cells),
-                                  cells.ctypes.data_as(_P(C.c_int64)), C.byref(s))
+        nreal = np.zeros(n) if with_nreal else None
+        rc = lib().orc_init_cells_nreal(C.byref(self.dom), _dp(np.ascontiguousarray(th, np.float64).ravel()),
+                                        _dp(np.ascontiguousarray(rv, np.float64).ravel()),
+                                        _dp(np.ascontiguousarray(rhod, np.float64).ravel()), len(cells),
+                                        cells.ctypes.data_as(_P(C.c_int64)), C.byref(s), _dp(nreal))
         if rc != 0:
             raise RuntimeError(f"orc_init_cells failed ({rc})")
-        return st
+        return (st, nreal) if with_nreal else st
 
     def init(self, th, rv, rhod):
         self.th = np.array(th, np.float64).ravel().copy()
         self.rv = np.array(rv, np.float64).ravel().copy()
         self.rhod = np.array(rhod, np.float64).ravel().copy()
-        self.state = self.init_cells(self.th, self.rv, self.rhod, np.arange(self.n_cells))
+        self.state, self.nreal = self.init_cells(self.th, self.rv, self.rhod, np.arange(self.n_cells),
+                                                 with_nreal=True)
         return self.state
 
     def step_sync(self, opts: dict | None = None):

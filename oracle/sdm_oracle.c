@@ -326,6 +326,15 @@ int orc_rd_range(const orc_domain *d, int group, double *lnr_min, double *lnr_ma
 int orc_init_cells(const orc_domain *d, const double *th, const double *rv, const double *rhod,
                    int64_t n_list, const int64_t *cells, orc_sds *out)
 {
+    return orc_init_cells_nreal(d, th, rv, rhod, n_list, cells, out, NULL);
+}
+
+/* The same, also returning (if nreal != NULL) each multiplicity before
+ * rounding, so that tests can tell rounding-ambiguous values apart. */
+int orc_init_cells_nreal(const orc_domain *d, const double *th, const double *rv,
+                         const double *rhod, int64_t n_list, const int64_t *cells, orc_sds *out,
+                         double *nreal)
+{
     double kap[ORC_MAX_MODES], lmin[ORC_MAX_MODES], lmax[ORC_MAX_MODES];
     int G = group_kappas(d, kap);
     if (d->init_dist == 0)
@@ -356,15 +365,19 @@ int orc_init_cells(const orc_domain *d, const double *th, const double *rv, cons
                     out->rw2[o] = r * r;
                     out->rd3[o] = 0.0;
                     out->kappa[o] = 0.0;
-                    double n = floor(d->exp_n0 * dV / d->sd_conc + 0.5);
+                    double v = d->exp_n0 * dV / d->sd_conc;
+                    double n = floor(v + 0.5);
                     out->N[o] = n < 1.0 ? 1 : (uint64_t)n;
+                    if (nreal) nreal[o] = v;
                 } else {
                     double lnr = lmin[g] + orc_u01(w[3]) * (lmax[g] - lmin[g]);
                     double rd = exp(lnr);
                     double rd3 = rd * rd * rd;
                     double dlnr = (lmax[g] - lmin[g]) / d->sd_conc;
-                    double n = floor(n_lnr(d, kap[g], lnr) * dlnr * dV * rhod[c] / rho_stp() + 0.5);
+                    double v = n_lnr(d, kap[g], lnr) * dlnr * dV * rhod[c] / rho_stp();
+                    double n = floor(v + 0.5);
                     out->N[o] = n < 1.0 ? 1 : (uint64_t)n;
+                    if (nreal) nreal[o] = v;
                     out->rd3[o] = rd3;
                     out->kappa[o] = kap[g];
                     out->rw2[o] = orc_equilibrium_rw2(rd3, kap[g], RH, t.T);

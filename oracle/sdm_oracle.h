@@ -83,6 +83,9 @@ double orc_equilibrium_rw2(double rd3, double kappa, double RH, double T);
 int orc_rd_range(const orc_domain *d, int group, double *lnr_min, double *lnr_max);
 int orc_init_cells(const orc_domain *d, const double *th, const double *rv, const double *rhod,
                    int64_t n_list, const int64_t *cells, orc_sds *out);
+int orc_init_cells_nreal(const orc_domain *d, const double *th, const double *rv,
+                         const double *rhod, int64_t n_list, const int64_t *cells, orc_sds *out,
+                         double *nreal);
 
 void orc_condense(const orc_domain *d, const orc_opts *o, orc_sds *s, double *th, double *rv,
                   const double *rhod, orc_stats *st);

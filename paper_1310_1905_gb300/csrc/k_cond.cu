@@ -7,7 +7,7 @@
 
 namespace sdm {
 
-__device__ __forceinline__ double fres(double x, double x0, double rd3, double kappa,
+SDM_HD double fres(double x, double x0, double rd3, double kappa,
                                        const Thermo &t, double dtp, int physics) {
     return x - x0 - dtp * growth(x, rd3, kappa, t, physics);
 }
@@ -15,7 +15,7 @@ __device__ __forceinline__ double fres(double x, double x0, double rd3, double k
 // The paper's predictor-corrector: bracket [a, b] from the derivative at
 // x0 with the factor 2, the Euler step (a+b)/2 when f does not change strict
 // sign over it, bisection to b - a <= 2^-52 b otherwise.
-__device__ double solve_rw2_bisect(double x0, double rd3, double kappa, const Thermo &t,
+__host__ __device__ double solve_rw2_bisect(double x0, double rd3, double kappa, const Thermo &t,
                                    double dtp, int physics, int *euler) {
     const double g0 = growth(x0, rd3, kappa, t, physics);
     const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
@@ -39,6 +39,170 @@ __device__ double solve_rw2_bisect(double x0, double rd3, double kappa, const Th
     return 0.5 * (lo + hi);
 }
 
+// ---------------------------------------------------------------------------
+// Bisection-faithful fast solve.  The bracket, the ill-posedness test and the
+// sequence of midpoints are exactly those of solve_rw2_bisect (FP64 interval
+// arithmetic), but the sign of f at a point is first computed in FP32 with
+// an error bound and trusted when |f| exceeds it; only when FP32 cannot tell
+// (the bracket has shrunk to FP32 resolution) is f evaluated in FP64.  From
+// there a bracketed Newton/secant iteration in FP64 converges to the single
+// sign change inside the current bracket, the same point the remaining
+// halvings of the paper's bisection converge to.  Iterates that leave the
+// bracket are replaced by its midpoint; if the iteration does not settle the
+// exact bisection finishes the job.
+struct ThermoF {
+    float rho_vs, rho_v_eff, A, Dterm, lambda_D, lambda_K, Sc, Pr, cX;
+};
+
+SDM_HD ThermoF to_float(const Thermo &t) {
+    ThermoF f;
+    f.rho_vs = (float)t.rho_vs;
+    f.rho_v_eff = (float)t.rho_v_eff;
+    f.A = (float)t.A;
+    f.Dterm = (float)t.Dterm;
+    f.lambda_D = (float)t.lambda_D;
+    f.lambda_K = (float)t.lambda_K;
+    f.Sc = (float)t.Sc;
+    f.Pr = (float)t.Pr;
+    f.cX = (float)t.cX;
+    return f;
+}
+
+SDM_HD float fs_f(float Kn) {
+    return (1.0f + Kn) / (1.0f + (4.0f / 3.0f + 0.377f) * Kn + 4.0f / 3.0f * Kn * Kn);
+}
+
+// FP32 growth rate g, an absolute error bound for it, and (optionally) an
+// approximate derivative dg/dx that ignores the slow variation of D_eff.
+SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t,
+                                          int physics, float *err, float *dgdx) {
+    const float r = sqrtf(x);
+    const float r3 = x * r;
+    const float num = r3 - rd3, den = r3 - rd3 * (1.0f - kappa);
+    const float aw = num / den;
+    const float Ar = t.A / r;
+    const float kel = expf(Ar);
+    const float rho_o = t.rho_vs * aw * kel;
+    float D = (float)phys::D0, K = (float)phys::K0;
+    if (physics) {
+        const float bM = fs_f(t.lambda_D / r), bT = fs_f(t.lambda_K / r);
+        const float X = t.cX * r3;
+        const float c1 = (float)(4.0 / (phys::delta0 * phys::delta0 * 0.54037024344425184));  // sqrt(C0)
+        const float e = c1 * sqrtf(X);
+        const float s = e / (sqrtf(1.0f + e) + 1.0f);
+        const float Re = (float)(phys::delta0 * phys::delta0 / 4.0) * s * s;
+        const float fRe = Re > 1.0f ? powf(Re, 0.077f) : 1.0f;
+        D = (float)phys::D0 * bM * (1.0f + cbrtf(1.0f + Re * t.Sc) * fRe) * 0.5f;
+        K = (float)phys::K0 * bT * (1.0f + cbrtf(1.0f + Re * t.Pr) * fRe) * 0.5f;
+    }
+    const float Deff = 1.0f / (1.0f / D + t.Dterm / K);
+    const float c = 2.0f * Deff / (float)phys::rho_w;
+    const float g = c * (t.rho_v_eff - rho_o);
+    // rounding of the difference's terms (a_w amplified where r ~ r_d) and
+    // of the D_eff factor, with a safety factor
+    const float amp = (r3 + rd3) / fmaxf(fabsf(num), 1e-37f);
+    const float eps = 5.9604645e-8f;  // 2^-24
+    *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 4.0f * Ar)) + 64.0f * fabsf(g));
+    if (dgdx) {
+        const float drho_dr = t.rho_vs * kel * (3.0f * r * r * rd3 * kappa / (den * den) - aw * t.A / (r * r));
+        *dgdx = -c * drho_dr / (2.0f * r);
+    }
+    return g;
+}
+
+struct SolveCounters {
+    int euler, fallback;
+};
+
+__host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
+                                 const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
+    const double g0 = growth(x0, rd3, kappa, t, physics);
+    const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
+    const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
+    const float rd3f = (float)rd3, kf = (float)kappa, dtpf = (float)dtp;
+    // sign of f(x) > 0, exactly as an FP64 evaluation would decide it
+    auto positive = [&](double x, bool *decided) -> bool {
+        *decided = true;
+        if (x == x0) return (x - x0) - dtp * g0 > 0.0;
+        const double d = x - x0;
+        float eg;
+        const float g = growth_f((float)x, rd3f, kf, tf, physics, &eg, nullptr);
+        const float f = (float)d - dtpf * g;
+        const float e = 2.4e-7f * fabsf((float)d) + 4.0f * dtpf * eg;
+        if (fabsf(f) > e) return f > 0.0f;
+        *decided = false;
+        return false;
+    };
+    auto positive64 = [&](double x) -> bool {
+        return fres(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
+    };
+    bool ok;
+    bool pa = positive(a, &ok);
+    if (!ok) pa = positive64(a);
+    bool pb = positive(b, &ok);
+    if (!ok) pb = positive64(b);
+    if (pa == pb) {
+        cnt.euler++;
+        return 0.5 * (a + b);
+    }
+    double lo = a, hi = b;
+    const bool plo = pa;
+    double mid = 0.0;
+    bool polish = false;
+    int it = 0;
+    for (; it < 200; ++it) {
+        if (hi - lo <= 0x1p-52 * hi) return 0.5 * (lo + hi);
+        mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) return 0.5 * (lo + hi);
+        const bool pm = positive(mid, &ok);
+        if (!ok) {
+            polish = true;
+            break;
+        }
+        if (pm == plo) lo = mid;
+        else hi = mid;
+    }
+    if (!polish) return 0.5 * (lo + hi);
+    // FP64 polish inside [lo, hi], keeping the bracket with exact signs
+    double xk = mid, fk = fres(xk, x0, rd3, kappa, t, dtp, physics);
+    double xp = 0.0, fp = 0.0;
+    bool have_prev = false;
+    for (int k = 0; k < 12; ++k) {
+        if (fk == 0.0) return xk;
+        if ((fk > 0.0) == plo) lo = xk;
+        else hi = xk;
+        if (hi - lo <= 0x1p-48 * hi) return 0.5 * (lo + hi);
+        double xn;
+        if (have_prev && fk != fp) {
+            xn = xk - fk * (xk - xp) / (fk - fp);  // secant
+        } else {
+            float eg, dg;
+            growth_f((float)xk, rd3f, kf, tf, physics, &eg, &dg);
+            const double fpr = 1.0 - dtp * (double)dg;  // approximate f'
+            xn = fpr != 0.0 ? xk - fk / fpr : 0.5 * (lo + hi);
+        }
+        // a step past an end of the bracket says the root hugs that end
+        if (!(xn < hi)) xn = hi - (hi - lo) * 0.015625;
+        if (!(xn > lo)) xn = lo + (hi - lo) * 0.015625;
+        if (fabs(xn - xk) <= 0x1p-50 * xk) return xn;
+        xp = xk;
+        fp = fk;
+        have_prev = true;
+        xk = xn;
+        fk = fres(xk, x0, rd3, kappa, t, dtp, physics);
+    }
+    // did not settle: finish with the exact bisection in the current bracket
+    cnt.fallback++;
+    for (; it < 200; ++it) {
+        if (hi - lo <= 0x1p-52 * hi) break;
+        const double m = 0.5 * (lo + hi);
+        if (!(m > lo && m < hi)) break;
+        if (positive64(m) == plo) lo = m;
+        else hi = m;
+    }
+    return 0.5 * (lo + hi);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -47,7 +211,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
                            const double *rhod, Grid g, int sstp, double RH_max, int physics,
-                           DevStats *st) {
+                           int solver, DevStats *st) {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= g.n_cells) return;
@@ -56,18 +220,24 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
     double thc = th[c], rvc = rv[c];
     const double rd = rhod[c];
     const double dtp = g.dt / sstp;
-    int n_euler = 0;
+    SolveCounters cnt{0, 0};
     bool bad = false;
     for (int sub = 0; sub < sstp; ++sub) {
         const Thermo t = thermo_eval(thc, rvc, rd, RH_max);
+        const ThermoF tf = to_float(t);
         double sum = 0.0;
         for (uint32_t i = beg + lane; i < end; i += 32) {
             const unsigned long long N = s.N[i];
             if (N == 0) continue;
             const double x0 = s.rw2[i];
-            int eu = 0;
-            const double x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, physics, &eu);
-            n_euler += eu;
+            double x1;
+            if (solver == 0) {
+                int eu = 0;
+                x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, physics, &eu);
+                cnt.euler += eu;
+            } else {
+                x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
+            }
             bad |= !isfinite(x1);
             s.rw2[i] = x1;
             sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
@@ -78,12 +248,14 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
         thc = t.th + drv * t.dth_drv;
     }
     bad |= !isfinite(rvc) || !isfinite(thc);
-    unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)n_euler);
+    const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
+    const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
     const unsigned anybad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
         th[c] = thc;
         rv[c] = rvc;
         if (ne) atomicAdd(&st->n_euler, (unsigned long long)ne);
+        if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
         if (anybad) atomicOr(&st->flags, kFlagNumeric);
     }
 }
@@ -93,7 +265,7 @@ cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
     const int64_t threads = (int64_t)c->grid.n_cells * 32;
     k_condense<<<grid_for(threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, c->th, c->rv,
                                                           c->rhod, c->grid, o.sstp_cond, o.RH_max,
-                                                          c->oi.physics, c->dstats);
+                                                          c->oi.physics, c->oi.cond_solver, c->dstats);
     return cudaGetLastError();
 }
 

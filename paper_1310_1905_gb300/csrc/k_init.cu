@@ -21,7 +21,7 @@ __device__ double n_lnr(const InitParams &p, double kap, double lnr) {
         if (p.mkappa[m] != kap) continue;
         const double ls = p.lsig[m];
         const double q = (lnr - p.lrm[m]) / ls;
-        s += p.n_stp[m] / (sqrt(2.0 * phys::pi) * ls) * exp(-0.5 * q * q);
+        s = __dadd_rn(s, __dmul_rn(p.n_stp[m] / (sqrt(2.0 * phys::pi) * ls), exp(-0.5 * q * q)));
     }
     return s;
 }
@@ -73,7 +73,9 @@ __global__ void k_init(SdArrays s, int64_t n, InitParams p, const double *th, co
         return;
     }
     const double lmin = p.lmin[grp], lmax = p.lmax[grp];
-    const double lnr = lmin + u01(w.v[3]) * (lmax - lmin);
+    // no fused multiply-add here: the lognormal's slope amplifies a one-ulp
+    // change of ln r about a hundredfold in the multiplicity
+    const double lnr = __dadd_rn(lmin, __dmul_rn(u01(w.v[3]), lmax - lmin));
     const double rd = exp(lnr);
     const double rd3 = rd * rd * rd;
     const double dlnr = (lmax - lmin) / p.sd_conc;

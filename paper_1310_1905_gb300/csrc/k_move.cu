@@ -211,12 +211,20 @@ __global__ void k_perm(const uint32_t *newcell, const uint32_t *slot, const uint
     if (q < n) perm[offset[newcell[q]] + slot[q]] = (uint32_t)q;
 }
 
-cudaError_t launch_regroup(sdm_ctx *c) {
-    const int n = c->grid.n_cells;
+// exclusive scan of n counts into offset[0..n], offset[n] = total;
+// tmp holds n/1024 + 2 words
+cudaError_t scan_counts(const uint32_t *count, uint32_t *offset, uint32_t *tmp, int n,
+                        cudaStream_t st) {
     const int nb = (n + kScanB - 1) / kScanB;
-    k_scan_local<<<nb, kScanB, 0, c->stream>>>(c->count, c->offset, c->scan_tmp, n);
-    k_scan_top<<<1, kScanB, 0, c->stream>>>(c->scan_tmp, nb, c->offset, n);
-    k_scan_add<<<nb, kScanB, 0, c->stream>>>(c->offset, c->scan_tmp, n);
+    k_scan_local<<<nb, kScanB, 0, st>>>(count, offset, tmp, n);
+    k_scan_top<<<1, kScanB, 0, st>>>(tmp, nb, offset, n);
+    k_scan_add<<<nb, kScanB, 0, st>>>(offset, tmp, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regroup(sdm_ctx *c) {
+    cudaError_t e = scan_counts(c->count, c->offset, c->scan_tmp, c->grid.n_cells, c->stream);
+    if (e != cudaSuccess) return e;
     const int B = 256;
     k_perm<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->newcell, c->slot, c->offset, c->perm,
                                                        c->n_sd);

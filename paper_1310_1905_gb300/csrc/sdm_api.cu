@@ -309,6 +309,8 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
         return fail(nullptr, SDM_EINVAL, "unknown collision kernel");
     if (oi->precision != SDM_PRECISION_FP64 && oi->precision != SDM_PRECISION_MIXED)
         return fail(nullptr, SDM_EINVAL, "unknown precision mode");
+    if (oi->cond_solver != SDM_SOLVER_BISECT && oi->cond_solver != SDM_SOLVER_FAST)
+        return fail(nullptr, SDM_EINVAL, "unknown condensation solver");
     if (oi->init_dist == SDM_INIT_LOGNORMAL) {
         if (oi->n_modes < 1 || oi->n_modes > kMaxModes || !oi->modes)
             return fail(nullptr, SDM_EINVAL, "lognormal initialisation needs 1..8 modes");

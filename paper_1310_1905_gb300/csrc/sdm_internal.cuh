@@ -15,6 +15,8 @@
 
 #include "../../include/sdm.h"
 
+#define SDM_HD __host__ __device__ __forceinline__
+
 namespace sdm {
 
 // ---------------------------------------------------------------- constants
@@ -70,7 +72,7 @@ __device__ __forceinline__ u64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c
 }
 
 // open-interval (0,1) uniform: 52 random bits plus one half, times 2^-52
-__device__ __forceinline__ double u01(uint64_t v) {
+SDM_HD double u01(uint64_t v) {
     return ((double)(v >> 12) + 0.5) * 0x1p-52;
 }
 
@@ -82,7 +84,7 @@ struct Thermo {
 };
 
 // Appendix A: T and p from theta, r_v, rho_d; Sec. 5.1.3 quantities.
-__device__ __forceinline__ Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
+SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
     using namespace phys;
     Thermo t;
     t.th = th;
@@ -111,7 +113,7 @@ __device__ __forceinline__ Thermo thermo_eval(double th, double rv, double rhod,
 }
 
 // Khvorostyanov & Curry (2002) sphere: Re(X), X = cX r^3 (Best number)
-__device__ __forceinline__ double reynolds(double rw2, double cX) {
+SDM_HD double reynolds(double rw2, double cX) {
     using namespace phys;
     const double r = sqrt(rw2);
     if (!(r > 0.0)) return 0.0;
@@ -123,18 +125,18 @@ __device__ __forceinline__ double reynolds(double rw2, double cX) {
 }
 
 // terminal velocity v_t = Re nu / (2 r)
-__device__ __forceinline__ double vterm(double rw2, double nu, double cX) {
+SDM_HD double vterm(double rw2, double nu, double cX) {
     const double r = sqrt(rw2);
     if (!(r > 0.0)) return 0.0;
     return reynolds(rw2, cX) * nu / (2.0 * r);
 }
 
-__device__ __forceinline__ double fuchs_sutugin(double Kn) {
+SDM_HD double fuchs_sutugin(double Kn) {
     return (1.0 + Kn) / (1.0 + (4.0 / 3.0 + 0.377) * Kn + 4.0 / 3.0 * Kn * Kn);
 }
 
 // dr_w^2/dt = 2 D_eff / rho_w (rho_v - rho_o), eq. (maxmason), (rho_circ)
-__device__ __forceinline__ double growth(double x, double rd3, double kappa, const Thermo &t,
+SDM_HD double growth(double x, double rd3, double kappa, const Thermo &t,
                                          int physics) {
     using namespace phys;
     const double r = sqrt(x);
@@ -156,7 +158,7 @@ __device__ __forceinline__ double growth(double x, double rd3, double kappa, con
     return 2.0 * Deff / rho_w * (t.rho_v_eff - rho_o);
 }
 
-__device__ __forceinline__ double rd2_of(double rd3) {
+SDM_HD double rd2_of(double rd3) {
     const double rd = cbrt(rd3);
     return rd * rd;
 }
@@ -251,6 +253,9 @@ cudaError_t launch_field_gather(double *dst, const double *src, const int64_t *s
                                 const int *shape, cudaStream_t s);
 cudaError_t launch_field_scatter(double *dst, const double *src, const int64_t *strides,
                                  int ndim, const int *shape, cudaStream_t s);
+
+cudaError_t scan_counts(const uint32_t *count, uint32_t *offset, uint32_t *tmp, int n,
+                        cudaStream_t st);
 
 // sort of (key_hi, key_lo, payload) records ascending by (key_hi, key_lo)
 struct SortRec {

@@ -29,6 +29,7 @@ KERNEL = {"geometric": 0, "golovin": 1}
 INIT = {"lognormal": 0, "exponential": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 BACKEND = {"serial": 0, "openmp": 1, "cuda": 2}
+SOLVER = {"bisect": 0, "fast": 1}
 ATTR = {"N": 0, "rw2": 1, "rd3": 2, "kappa": 3, "x": 4, "y": 5, "z": 6, "uid": 7}
 ATTR_DTYPE = {"N": np.uint64, "uid": np.uint32}
 
@@ -49,6 +50,7 @@ class sdm_opts_init(C.Structure):
         ("init_dist", C.c_int), ("exp_mean_volume", C.c_double), ("exp_n0", C.c_double),
         ("n_modes", C.c_int), ("modes", C.POINTER(sdm_lognormal)),
         ("seed", C.c_uint64), ("physics", C.c_int), ("precision", C.c_int), ("backend", C.c_int),
+        ("cond_solver", C.c_int),
     ]
 
 
@@ -164,6 +166,7 @@ def make_opts_init(cfg: dict, precision: str = "fp64", backend: str = "cuda"):
     o.physics = cfg.get("physics", 1)
     o.precision = PRECISION[precision]
     o.backend = BACKEND[backend]
+    o.cond_solver = SOLVER[cfg.get("cond_solver", "fast")]
     return o, arr
 
 

@@ -19,6 +19,13 @@ def oracle_sim(w):
     return o
 
 
+def pair(w, precision="fp64"):
+    """GPU particles and oracle on the same inputs, same initial integers."""
+    p, o = gpu_particles(w, precision), oracle_sim(w)
+    start_from_oracle_multiplicities(p, o)
+    return p, o
+
+
 def oracle_state(o, present=("x", "z")):
     s = o.state.sorted_by_uid()
     out = {"uid": s.uid, "N": s.N, "rw2": s.rw2, "rd3": s.rd3, "kappa": s.kappa}
@@ -43,10 +50,32 @@ def assert_close(name, got, ref, rtol=RTOL, atol=0.0):
                              f"got {got[i]!r} ref {ref[i]!r} rel {err[i] / max(abs(ref[i]), 1e-300):.3e}")
 
 
-def compare_states(g, r, rtol=RTOL, exact_N=True):
+def start_from_oracle_multiplicities(p, o):
+    """Initial multiplicities are floor(v + 1/2) of an FP64 value v computed
+    with exp() on both sides; where v lies within a few ulps of a half-integer
+    the two sides may round differently (checked by the init tests).  The
+    dynamics tests therefore start the GPU from the oracle's integers."""
+    uid = p.attr("uid").astype(np.int64)
+    order = np.argsort(o.state.uid)
+    N_by_uid = o.state.N[order]
+    sdm.sdm_set_attr(p.ctx, "N", N_by_uid[uid])
+
+
+def rounding_ambiguous(v):
+    """True where floor(v + 1/2) may flip under a few ulps of v."""
+    v = np.asarray(v, np.float64)
+    return np.abs(v - np.floor(v) - 0.5) <= 16 * np.spacing(v)
+
+
+def compare_states(g, r, rtol=RTOL, exact_N=True, nreal=None):
     assert np.array_equal(g["uid"], r["uid"].astype(g["uid"].dtype))
     if exact_N:
         bad = np.nonzero(g["N"] != r["N"])[0]
+        if nreal is not None and bad.size:
+            # an init comparison: only rounding-ambiguous values may differ, by one
+            assert rounding_ambiguous(nreal[bad]).all(), "a multiplicity differs away from a rounding tie"
+            assert (np.abs(g["N"][bad].astype(np.int64) - r["N"][bad].astype(np.int64)) == 1).all()
+            bad = bad[:0]
         assert bad.size == 0, f"multiplicities differ for {bad.size} super-droplets, first ids {g['uid'][bad[:5]]}: " \
                               f"gpu {g['N'][bad[:5]]} oracle {r['N'][bad[:5]]}"
     for k in ("rw2", "rd3", "kappa"):

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import (RTOL, assert_close, compare_states, gpu_particles, oracle_sim, oracle_state,
+from gpu_helpers import (RTOL, assert_close, compare_states, gpu_particles, oracle_sim, oracle_state, pair,
                          present_dims)
 from paper_1310_1905_gb300 import sdm
 
@@ -27,7 +27,16 @@ def test_init_matches_oracle(seed):
     w = small_2d(seed)
     p = gpu_particles(w)
     o = oracle_sim(w)
-    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)), nreal=o.nreal)
+
+
+def test_init_large_multiplicities_3d():
+    # 150 m cubes: multiplicities ~1e14, where an ulp of the FP64 value is
+    # ~0.03 and ties to the rounding boundary really occur
+    w = workloads.updraft_3d(nx=4, ny=3, nz=9, sd_conc=10, seed=8, dx=150.0)
+    p = gpu_particles(w)
+    o = oracle_sim(w)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)), nreal=o.nreal)
 
 
 def test_init_golovin_box():
@@ -37,9 +46,11 @@ def test_init_golovin_box():
     compare_states(p.state(), oracle_state(o, ()))
 
 
-def test_condensation_matches_oracle():
+@pytest.mark.parametrize("solver", ["fast", "bisect"])
+def test_condensation_matches_oracle(solver):
     w = small_2d(3)
-    p, o = gpu_particles(w), oracle_sim(w)
+    w.cfg["cond_solver"] = solver
+    p, o = pair(w)
     th, rv = w.th.copy(), w.rv.copy()
     for _ in range(4):
         p.step_sync(COND_ONLY, th, rv)
@@ -52,7 +63,7 @@ def test_condensation_matches_oracle():
 
 def test_condensation_bare_maxwell_mason():
     w = workloads.icmw_2d(nx=5, nz=11, sd_conc=12, seed=4, dz=130.0, physics=0)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     th, rv = w.th.copy(), w.rv.copy()
     for _ in range(3):
         p.step_sync(COND_ONLY, th, rv)
@@ -64,7 +75,7 @@ def test_condensation_bare_maxwell_mason():
 
 def test_transport_matches_oracle():
     w = small_2d(5)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     for _ in range(6):
         p.step_async(MOVE_ONLY)
         rain_g = p.wait()
@@ -76,7 +87,7 @@ def test_transport_matches_oracle():
 def test_coalescence_golovin_box_full_run():
     """Config: Golovin box, 8192 super-droplets, 1 s steps, 3600 s."""
     w = workloads.golovin_box(seed=2)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     for t in range(1, 3601):
         p.step_async(w.opts)
         p.wait()
@@ -91,7 +102,7 @@ def test_coalescence_golovin_box_full_run():
 
 def test_coalescence_geometric_2d():
     w = small_2d(6, sd=40)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     # grow big drops first so that collisions happen: condense for a while
     th, rv = w.th.copy(), w.rv.copy()
     for _ in range(3):
@@ -107,7 +118,7 @@ def test_coalescence_geometric_2d():
 
 def test_full_steps_2d():
     w = small_2d(7)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     th, rv = w.th.copy(), w.rv.copy()
     for _ in range(8):
         p.step_sync(ALL, th, rv)
@@ -124,7 +135,7 @@ def test_full_steps_2d():
 
 def test_full_steps_3d_small():
     w = workloads.updraft_3d(nx=4, ny=3, nz=9, sd_conc=10, seed=8, dx=150.0)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     th, rv = w.th.copy(), w.rv.copy()
     for _ in range(6):
         p.step_sync(ALL, th, rv)
@@ -139,7 +150,7 @@ def test_full_steps_3d_small():
 
 def test_recycling_matches_oracle():
     w = small_2d(9)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     # zero out a pseudo-random fifth of the multiplicities on both sides
     g = p.state()
     rng = np.random.default_rng(0)
@@ -162,7 +173,7 @@ def test_recycling_matches_oracle():
 
 def test_diagnostics_match_oracle():
     w = small_2d(10)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     th, rv = w.th.copy(), w.rv.copy()
     p.step_sync(COND_ONLY, th, rv)
     o.step_sync(COND_ONLY)
@@ -176,7 +187,7 @@ def test_diagnostics_match_oracle():
 def test_device_resident_fields_and_strides():
     torch = pytest.importorskip("torch")
     w = small_2d(11)
-    p, o = gpu_particles(w), oracle_sim(w)
+    p, o = pair(w)
     # fields on the device, transposed storage (strides (1, nx))
     th = torch.tensor(w.th.T.copy(), dtype=torch.float64, device="cuda").t()
     rv = torch.tensor(w.rv.T.copy(), dtype=torch.float64, device="cuda").t()
