@@ -257,6 +257,92 @@ sdm_status sdm_get_stats(sdm_ctx *ctx, sdm_stats *out);
 sdm_status sdm_timing_enable(sdm_ctx *ctx, int on);
 sdm_status sdm_get_timing(sdm_ctx *ctx, sdm_timing *out, int reset);
 
+/* ---- batched ensembles of 0D members -------------------------------------
+ * Many independent box or adiabatic-parcel simulations (the particles_t
+ * parcel set-up, nx = ny = nz = 0, Sec. 5.2.1) advanced together by one set
+ * of launches per step, capturable as one CUDA graph.  Each member draws its
+ * random numbers from its own seed, ids and step count, so its result does
+ * not depend on which other members share the batch.  Parcels conserve
+ * their dry-air mass: a new rho_d changes their volume to m_d / rho_d. */
+typedef struct sdm_ens sdm_ens;
+
+/* One member.  n_sd super-droplets in one cell of volume dV [m^3] at theta,
+ * r_v, rho_d; initial spectrum as in sdm_opts_init (1..4 lognormal modes
+ * that share one kappa, or the exponential box spectrum); seed keys its
+ * random numbers. */
+typedef struct {
+    int64_t n_sd;
+    double dV;
+    double th, rv, rhod;
+    int init_dist;
+    int n_modes;
+    sdm_lognormal modes[4];
+    double exp_mean_volume, exp_n0;
+    uint64_t seed;
+} sdm_member;
+
+/* Options shared by the members (see sdm_opts_init) and the capacity of the
+ * device arena: at most max_sd super-droplets and max_members members are
+ * resident at a time; sdm_ens_create reserves the memory for them. */
+typedef struct {
+    double dt;
+    int kernel;
+    double golovin_b;
+    int physics, precision, cond_solver;
+    int64_t max_sd;
+    int32_t max_members;
+} sdm_ens_opts;
+
+sdm_status sdm_ens_create(const sdm_ens_opts *opts, void *stream, sdm_ens **out);
+sdm_status sdm_ens_destroy(sdm_ens *e);
+const char *sdm_ens_last_error(const sdm_ens *e);
+
+/* Admit a member (initialised on the device, Sec. 5.1.6); *id receives its
+ * handle.  SDM_ENOMEM when the arena cannot hold it (nothing changes). */
+sdm_status sdm_ens_add(sdm_ens *e, const sdm_member *m, int32_t *id);
+
+/* Retire a member; its memory is reused from the next step on. */
+sdm_status sdm_ens_remove(sdm_ens *e, int32_t id);
+
+/* Ids of the resident members (up to cap) and their count, and the number
+ * of resident super-droplets. */
+sdm_status sdm_ens_members(const sdm_ens *e, int32_t *ids, int32_t cap, int32_t *n, int64_t *n_sd);
+
+/* One full timestep of every resident member: recycling, sstp_cond
+ * condensation substeps with the per-member vapour/theta feedback,
+ * sstp_coal coalescence substeps (opts->adve and opts->sedi have no meaning
+ * in 0D).  ids/rhod (n entries, host memory, nullable) give a new rho_d for
+ * some members before the step (parcels).  Enqueues and returns. */
+sdm_status sdm_ens_step(sdm_ens *e, const sdm_opts *opts, const int32_t *ids, const double *rhod,
+                        int32_t n);
+
+/* Wait at most timeout_s seconds (< 0: no limit) for the last step. */
+sdm_status sdm_ens_wait(sdm_ens *e, double timeout_s);
+
+/* Per-member moments (as sdm_diag_mom, per unit dry-air mass) into host
+ * out[n] for the listed ids; completes before returning. */
+sdm_status sdm_ens_moments(sdm_ens *e, int wet, double r_min, double r_max, int k, const int32_t *ids,
+                           double *out, int32_t n);
+
+/* Current theta and r_v of the listed members (host arrays). */
+sdm_status sdm_ens_fields(sdm_ens *e, const int32_t *ids, double *th, double *rv, int32_t n);
+
+/* One attribute (SDM_ATTR_N, _RW2, _RD3, _KAPPA, _UID) of one member's
+ * super-droplets, in id order, into host dst (n = the member's n_sd). */
+sdm_status sdm_ens_get_attr(sdm_ens *e, int32_t id, int attr, void *dst, int64_t n);
+
+/* Replay steps from a captured CUDA graph (1) or launch them one by one
+ * (0, the default).  The graph is re-captured when membership or options
+ * change. */
+sdm_status sdm_ens_use_graph(sdm_ens *e, int on);
+
+/* Choose the condensation tile size and block shape by timing candidate
+ * shapes on the resident members (their state is restored afterwards). */
+sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *opts, int *tile_out, int *threads_out);
+
+/* Counters accumulated over all members since creation. */
+sdm_status sdm_ens_stats(sdm_ens *e, sdm_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ namespace sdm {
 
 struct CoalParams {
     Grid g;
-    int sstp, coal, kernel;
+    int sstp, coal, kernel, mixed;
     double golovin_b;
     uint64_t seed, step;
 };
@@ -92,6 +92,38 @@ __device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, dou
     const double ra = sqrt(rw2a), rb = sqrt(rw2b);
     const double dv = fabs(vta - vtb);
     return phys::pi * (ra + rb) * (ra + rb) * dv;
+}
+
+// Mixed-precision mode: terminal velocities, the kernel and P in FP32, a
+// 24-bit uniform number and 32-bit shuffle keys (ties still broken by id);
+// merged radii stay FP64 so that r^3 is conserved to FP64 rounding.
+__device__ __forceinline__ double vt_of(const CoalParams &p, double rw2, double nu, double cX) {
+    return p.mixed ? (double)vterm_f((float)rw2, (float)nu, (float)cX) : vterm(rw2, nu, cX);
+}
+
+__device__ __forceinline__ double prob(const CoalParams &p, unsigned long long Nmax, double rwa,
+                                       double rwb, double va, double vb, double dtpp, double scale) {
+    if (p.mixed) {
+        float K;
+        if (p.kernel == SDM_KERNEL_GOLOVIN) {
+            const float a = (float)rwa, b = (float)rwb;
+            K = (float)p.golovin_b * (4.0f / 3.0f * (float)phys::pi) * (a * sqrtf(a) + b * sqrtf(b));
+        } else {
+            const float ra = sqrtf((float)rwa), rb = sqrtf((float)rwb);
+            K = (float)phys::pi * (ra + rb) * (ra + rb) * fabsf((float)va - (float)vb);
+        }
+        return (double)((float)Nmax * K * (float)dtpp / (float)p.g.dV * (float)scale);
+    }
+    const double K = kernel_K(p, rwa, rwb, va, vb);
+    return (double)Nmax * K * dtpp / p.g.dV * scale;
+}
+
+__device__ __forceinline__ bool accepted(const CoalParams &p, uint64_t w, double P) {
+    return p.mixed ? u01f(w) < (float)P : u01(w) < P;
+}
+
+__device__ __forceinline__ unsigned long long key_of(const CoalParams &p, uint64_t w0) {
+    return p.mixed ? (w0 & 0xFFFFFFFF00000000ull) : w0;
 }
 
 // one collision event: the larger-N member (the first on a tie) keeps its
@@ -170,7 +202,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             W.rd3[q] = src.rd3[pi];
             W.kappa[q] = src.kappa[pi];
             W.uid[q] = id;
-            W.vt[q] = geo ? vterm(W.rw2[q], nu, cX) : 0.0;
+            W.vt[q] = geo ? vt_of(p, W.rw2[q], nu, cX) : 0.0;
             if (p.g.nx > 0) dst.x[beg + q] = src.x[pi];
             if (p.g.ny > 0) dst.y[beg + q] = src.y[pi];
             if (p.g.nz > 0) dst.z[beg + q] = src.z[pi];
@@ -192,7 +224,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 if (q < n && W.N[q] > 0) {
                     const u64x4 w = philox4x64(W.uid[q], (uint64_t)sub, p.step, kStreamCoal, p.seed, 0);
                     W.acc[q] = w.v[1];
-                    KeyRec kr{w.v[0], ((unsigned long long)W.uid[q] << 32) | (unsigned)q};
+                    KeyRec kr{key_of(p, w.v[0]), ((unsigned long long)W.uid[q] << 32) | (unsigned)q};
                     if (r) {
                         k1 = kr;
                         act1 = true;
@@ -209,15 +241,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
             if (2 * lane + 1 < m) {
                 const int a = (int)(k0.pk & 0xffu), b = (int)(k1.pk & 0xffu);
-                const double K = kernel_K(p, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b]);
                 const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
-                const double P = (double)Nmax * K * dtpp / p.g.dV * scale;
+                const double P = prob(p, Nmax, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b], dtpp, scale);
                 n_pairs++;
                 if (P > 1.0) n_pgt1++;
                 max_p = fmax(max_p, P);
-                if (u01(W.acc[a]) < P) {
+                if (accepted(p, W.acc[a], P)) {
                     const int S = collide(A, a, b);
-                    if (geo) W.vt[S] = vterm(W.rw2[S], nu, cX);
+                    if (geo) W.vt[S] = vt_of(p, W.rw2[S], nu, cX);
                     n_coll++;
                 }
             }
@@ -347,7 +378,7 @@ __global__ void __launch_bounds__(kBigBlock)
                     if (t < n && dst.N[beg + t] > 0) {
                         const uint32_t id = dst.uid[beg + t];
                         const u64x4 w = philox4x64(id, (uint64_t)sub, p.step, kStreamCoal, p.seed, 0);
-                        skey[t] = w.v[0];
+                        skey[t] = key_of(p, w.v[0]);
                         sacc[t] = w.v[1];
                         spk[t] = ((unsigned long long)id << 32) | (unsigned)t;
                         my_m++;
@@ -370,15 +401,14 @@ __global__ void __launch_bounds__(kBigBlock)
                 for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
                     const int a = (int)(spk[2 * k] & 0xffffffffu), b = (int)(spk[2 * k + 1] & 0xffffffffu);
                     const double rwa = A.rw2(a), rwb = A.rw2(b);
-                    const double K = kernel_K(p, rwa, rwb, geo ? vterm(rwa, nu, cX) : 0.0,
-                                              geo ? vterm(rwb, nu, cX) : 0.0);
                     const unsigned long long Na = A.N(a), Nb = A.N(b);
                     const unsigned long long Nmax = Na > Nb ? Na : Nb;
-                    const double P = (double)Nmax * K * dtpp / p.g.dV * scale;
+                    const double P = prob(p, Nmax, rwa, rwb, geo ? vt_of(p, rwa, nu, cX) : 0.0,
+                                          geo ? vt_of(p, rwb, nu, cX) : 0.0, dtpp, scale);
                     np++;
                     if (P > 1.0) ng++;
                     mp = fmax(mp, P);
-                    if (u01(sacc[a]) < P) {
+                    if (accepted(p, sacc[a], P)) {
                         collide(A, a, b);
                         nc++;
                     }
@@ -411,6 +441,7 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     p.sstp = o.sstp_coal;
     p.coal = coal ? 1 : 0;
     p.kernel = c->oi.kernel;
+    p.mixed = c->oi.precision == SDM_PRECISION_MIXED;
     p.golovin_b = c->oi.golovin_b;
     p.seed = c->oi.seed;
     p.step = c->step;

@@ -203,6 +203,63 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     return 0.5 * (lo + hi);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision solve: the same bracket and Euler rule, then a bracketed
+// Newton iteration, all in FP32 on the increment d = x - x0 (so that a small
+// change of a large r_w^2 is not lost to FP32 rounding of x itself).  The
+// new r_w^2 = x0 + d is formed in FP64.  Iterates never leave the bracket;
+// after 24 steps without settling the last one is used.
+__host__ __device__ bool solve_rw2_f32(double x0, double rd3, double kappa, const ThermoF &tf,
+                                       float dtp, int physics, double *x1, SolveCounters &cnt) {
+    const float rd3f = (float)rd3, kf = (float)kappa;
+    float eg, dg;
+    const float g0 = growth_f((float)x0, rd3f, kf, tf, physics, &eg, nullptr);
+    const float lo_d = fmaxf((float)(rd2_of(rd3) - x0), fminf(2.0f * dtp * g0, 0.0f));
+    const float hi_d = fmaxf(2.0f * dtp * g0, 0.0f);
+    auto f = [&](float d, float *der) -> float {
+        const float g = growth_f((float)(x0 + (double)d), rd3f, kf, tf, physics, &eg, der ? &dg : nullptr);
+        if (der) *der = 1.0f - dtp * dg;
+        return d - dtp * g;
+    };
+    const float fa = f(lo_d, nullptr), fb = f(hi_d, nullptr);
+    if ((fa > 0.0f) == (fb > 0.0f)) {
+        cnt.euler++;
+        *x1 = x0 + 0.5 * ((double)lo_d + (double)hi_d);
+        return true;
+    }
+    float lo = lo_d, hi = hi_d;
+    const bool plo = fa > 0.0f;
+    float d = 0.5f * (lo + hi);
+    for (int k = 0; k < 24; ++k) {
+        float der;
+        const float fd = f(d, &der);
+        if (fd == 0.0f) break;
+        if ((fd > 0.0f) == plo) lo = d;
+        else hi = d;
+        float dn = der != 0.0f ? d - fd / der : 0.5f * (lo + hi);
+        if (!(dn > lo && dn < hi)) dn = 0.5f * (lo + hi);
+        const float step = fabsf(dn - d);
+        d = dn;
+        if (step <= 1e-6f * fmaxf(fabsf(d), 1e-30f) || hi - lo <= 1e-6f * fmaxf(fabsf(hi), fabsf(lo))) {
+            *x1 = x0 + (double)d;
+            return true;
+        }
+    }
+    *x1 = x0 + (double)d;
+    return true;
+}
+
+// FP32 is kept away from droplets near Koehler activation in supersaturated
+// air, where the growth equation is stiff and the root sensitive: there the
+// FP64 solve runs.  r_crit^2 = 3 kappa r_d^3 / A (the kappa-Koehler critical
+// radius for a dilute solution).
+__host__ __device__ __forceinline__ bool near_activation(double x0, double rd3, double kappa,
+                                                         const Thermo &t) {
+    if (t.rho_v_eff < 0.99 * t.rho_vs) return false;
+    const double rc2 = 3.0 * kappa * rd3 / t.A;
+    return x0 < 9.0 * rc2;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -211,7 +268,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
                            const double *rhod, Grid g, int sstp, double RH_max, int physics,
-                           int solver, DevStats *st) {
+                           int solver, int mixed, DevStats *st) {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= g.n_cells) return;
@@ -231,7 +288,9 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
             if (N == 0) continue;
             const double x0 = s.rw2[i];
             double x1;
-            if (solver == 0) {
+            if (mixed && !near_activation(x0, s.rd3[i], s.kappa[i], t)) {
+                solve_rw2_f32(x0, s.rd3[i], s.kappa[i], tf, (float)dtp, physics, &x1, cnt);
+            } else if (solver == 0) {
                 int eu = 0;
                 x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, physics, &eu);
                 cnt.euler += eu;
@@ -260,12 +319,78 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
     }
 }
 
+// Ensemble condensation, one substep: a block per tile (tiles never straddle
+// two members), the member's thermodynamics computed once per block, a
+// deterministic block sum of N (r_w^3[new] - r_w^3[old]) into tile_sum.
+__global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,
+                                 const uint32_t *tile_beg, const uint32_t *tile_end, double *tile_sum,
+                                 EnsCondParams p, DevStats *st) {
+    __shared__ Thermo s_t;
+    __shared__ double s_part[32];
+    const int tile = blockIdx.x;
+    const MemberDev &md = M[tile_member[tile]];
+    if (threadIdx.x == 0) s_t = thermo_eval(md.th, md.rv, md.rhod, p.RH_max);
+    __syncthreads();
+    const Thermo t = s_t;
+    const ThermoF tf = to_float(t);
+    const double dtp = p.dt / p.sstp;
+    SolveCounters cnt{0, 0};
+    double sum = 0.0;
+    bool bad = false;
+    for (uint32_t i = tile_beg[tile] + threadIdx.x; i < tile_end[tile]; i += blockDim.x) {
+        const unsigned long long N = s.N[i];
+        if (N == 0) continue;
+        const double x0 = s.rw2[i];
+        double x1;
+        if (p.mixed && !near_activation(x0, s.rd3[i], s.kappa[i], t)) {
+            solve_rw2_f32(x0, s.rd3[i], s.kappa[i], tf, (float)dtp, p.physics, &x1, cnt);
+        } else if (p.solver == 0) {
+            int eu = 0;
+            x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, p.physics, &eu);
+            cnt.euler += eu;
+        } else {
+            x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, p.physics, cnt);
+        }
+        bad |= !isfinite(x1);
+        s.rw2[i] = x1;
+        sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+    }
+    sum = warp_sum(sum);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_part[w] = sum;
+    const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
+    const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
+    const unsigned anybad = __any_sync(0xffffffffu, bad);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int v = 0; v < (int)(blockDim.x >> 5); ++v) tsum += s_part[v];
+        tile_sum[tile] = tsum;
+    }
+    if (lane == 0) {
+        if (ne) atomicAdd(&st->n_euler, (unsigned long long)ne);
+        if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
+        if (anybad) atomicOr(&st->flags, kFlagNumeric);
+    }
+}
+
+cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,
+                                  const uint32_t *tile_beg, const uint32_t *tile_end, double *tile_sum,
+                                  int n_tiles, int threads, EnsCondParams p, DevStats *st,
+                                  cudaStream_t stream) {
+    if (n_tiles == 0) return cudaSuccess;
+    k_ens_cond_tiles<<<n_tiles, threads, 0, stream>>>(s, M, tile_member, tile_beg, tile_end, tile_sum, p,
+                                                       st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
     const int B = 128;
     const int64_t threads = (int64_t)c->grid.n_cells * 32;
     k_condense<<<grid_for(threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, c->th, c->rv,
                                                           c->rhod, c->grid, o.sstp_cond, o.RH_max,
-                                                          c->oi.physics, c->oi.cond_solver, c->dstats);
+                                                          c->oi.physics, c->oi.cond_solver,
+                                                          c->oi.precision == SDM_PRECISION_MIXED, c->dstats);
     return cudaGetLastError();
 }
 

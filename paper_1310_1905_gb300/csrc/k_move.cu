@@ -72,7 +72,7 @@ __device__ __forceinline__ double wrap(double x, double X) {
 
 struct MoveParams {
     Grid g;
-    int adve, sedi, transport;
+    int adve, sedi, transport, mixed;
     const double *Cx, *Cy, *Cz;
 };
 
@@ -87,7 +87,9 @@ __global__ void k_move(SdArrays s, int64_t n, MoveParams p, const double *rhod, 
         const int i = c / (g.NY * g.NZ), j = (c / g.NZ) % g.NY, k = c % g.NZ;
         double vt = 0.0;
         const bool sedi = p.sedi && g.nz > 0;
-        if (sedi) vt = vterm(s.rw2[q], amb[2 * c], amb[2 * c + 1]);
+        if (sedi)
+            vt = p.mixed ? (double)vterm_f((float)s.rw2[q], (float)amb[2 * c], (float)amb[2 * c + 1])
+                         : vterm(s.rw2[q], amb[2 * c], amb[2 * c + 1]);
         if (p.adve) {
             if (g.nx > 0 && p.Cx)
                 x = wrap(advect_1d(x, g.dx, i, courant_x(g, rhod, p.Cx, i, j, k),
@@ -132,6 +134,7 @@ cudaError_t launch_move(sdm_ctx *c, const sdm_opts &o) {
     p.g = c->grid;
     p.adve = o.adve;
     p.sedi = o.sedi;
+    p.mixed = c->oi.precision == SDM_PRECISION_MIXED;
     p.transport = o.adve || o.sedi;
     p.Cx = c->rhoC[0];
     p.Cy = c->rhoC[1];

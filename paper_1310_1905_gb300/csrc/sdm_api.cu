@@ -126,13 +126,20 @@ double n_lnr_host(const std::vector<sdm_lognormal> &modes, double kap, double ln
 }
 
 bool rd_range(const sdm_ctx *c, double kap, double *lo_out, double *hi_out) {
+    return sdm::rd_range_modes(c->modes, kap, c->oi.sd_conc, c->oi.dx * c->oi.dy * c->oi.dz, lo_out,
+                               hi_out);
+}
+
+}  // namespace
+
+bool sdm::rd_range_modes(const std::vector<sdm_lognormal> &modes, double kap, int64_t sd_conc, double dV,
+                         double *lo_out, double *hi_out) {
     const double L0 = log(1e-9), L1 = log(1e-5);
     const int NG = 1000;
-    const double dV = c->oi.dx * c->oi.dy * c->oi.dz;
     double lo = L0, hi = L1;
     for (int pass = 0; pass < 8; ++pass) {
-        const double dlnr = (hi - lo) / c->oi.sd_conc;
-        auto w = [&](double l) { return n_lnr_host(c->modes, kap, l) * dlnr * dV; };
+        const double dlnr = (hi - lo) / sd_conc;
+        auto w = [&](double l) { return n_lnr_host(modes, kap, l) * dlnr * dV; };
         int jlo = -1, jhi = -1;
         for (int j = 0; j <= NG; ++j)
             if (w(L0 + (L1 - L0) * j / NG) >= 1.0) {
@@ -171,6 +178,8 @@ bool rd_range(const sdm_ctx *c, double kap, double *lo_out, double *hi_out) {
     *hi_out = hi;
     return true;
 }
+
+namespace {
 
 template <class T>
 cudaError_t dalloc(T **p, size_t n) {
@@ -287,6 +296,8 @@ sdm_status check_opts(sdm_ctx *c, const sdm_opts *o) {
 }
 
 }  // namespace
+
+void sdm::sdm_set_global_error(const std::string &msg) { g_init_err = msg; }
 
 // ---------------------------------------------------------------- ABI
 extern "C" {

@@ -131,6 +131,21 @@ SDM_HD double vterm(double rw2, double nu, double cX) {
     return reynolds(rw2, cX) * nu / (2.0 * r);
 }
 
+// the same terminal velocity in FP32 (mixed-precision mode)
+SDM_HD float vterm_f(float rw2, float nu, float cX) {
+    const float r = sqrtf(rw2);
+    if (!(r > 0.0f)) return 0.0f;
+    const float X = cX * rw2 * r;
+    const float c1 = (float)(4.0 / (phys::delta0 * phys::delta0 * 0.54037024344425184));  // sqrt(C0)
+    const float e = c1 * sqrtf(X);
+    const float s = e / (sqrtf(1.0f + e) + 1.0f);
+    const float Re = (float)(phys::delta0 * phys::delta0 / 4.0) * s * s;
+    return Re * nu / (2.0f * r);
+}
+
+// 24 random bits plus one half, times 2^-24: open (0,1) in FP32
+SDM_HD float u01f(uint64_t v) { return ((float)(uint32_t)(v >> 40) + 0.5f) * 5.9604645e-8f; }
+
 SDM_HD double fuchs_sutugin(double Kn) {
     return (1.0 + Kn) / (1.0 + (4.0 / 3.0 + 0.377) * Kn + 4.0 / 3.0 * Kn * Kn);
 }
@@ -257,12 +272,46 @@ cudaError_t launch_field_scatter(double *dst, const double *src, const int64_t *
 cudaError_t scan_counts(const uint32_t *count, uint32_t *offset, uint32_t *tmp, int n,
                         cudaStream_t st);
 
+// ---- batched ensembles of 0D members (ens.cu)
+struct MemberDev {
+    uint32_t off, n;         // super-droplet range
+    uint32_t tile0, ntiles;  // condensation tiles
+    uint32_t active;         // super-droplets with N > 0 (per substep)
+    uint32_t zeros;
+    double dV, md;           // volume [m^3], dry-air mass [kg]
+    double th, rv, rhod;
+    unsigned long long seed, step;
+};
+
+struct EnsCondParams {
+    double dt;
+    int sstp, physics, solver, mixed;
+    double RH_max;
+};
+
+// one substep of condensation for every tile (k_cond.cu)
+cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,
+                                  const uint32_t *tile_beg, const uint32_t *tile_end, double *tile_sum,
+                                  int n_tiles, int threads, EnsCondParams p, DevStats *st,
+                                  cudaStream_t stream);
+cudaError_t cell_sort_with_scratch(const uint32_t *cell, int64_t n, uint32_t n_cells, uint32_t *perm,
+                                   uint32_t *offsets, uint32_t *count, uint32_t *slot,
+                                   uint32_t *scan_tmp, unsigned *bad, cudaStream_t st);
+
 // sort of (key_hi, key_lo, payload) records ascending by (key_hi, key_lo)
 struct SortRec {
     unsigned long long hi;
     uint32_t lo, val;
 };
 cudaError_t sort_records(SortRec *rec, uint32_t n, uint32_t n_pow2, cudaStream_t s);
+
+// message returned by sdm_last_error(NULL) on this thread
+void sdm_set_global_error(const std::string &msg);
+
+// initial dry-radius range of one kappa group (host; shared by contexts and
+// ensemble members): the outermost ln r where n(ln r) dlnr dV >= 1
+bool rd_range_modes(const std::vector<sdm_lognormal> &modes, double kap, int64_t sd_conc, double dV,
+                    double *lo_out, double *hi_out);
 
 inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)((n + block - 1) / block);
