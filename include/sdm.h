@@ -250,6 +250,24 @@ sdm_status sdm_set_step(sdm_ctx *ctx, uint64_t step);
 sdm_status sdm_cell_sort(const uint32_t *cell, int64_t n, int32_t n_cells, uint32_t *perm,
                          uint32_t *offsets, void *stream);
 
+/* The same sort for callers that cannot allocate device memory while they
+ * run (inside a captured CUDA graph, in a stream-ordered region where a
+ * cudaMalloc would synchronise, or under a memory pool fixed at start-up).
+ * The paper has no counterpart: this is a systems variant of the call above.
+ * It allocates nothing: its scratch is one fixed file-scope device array of
+ * about 10 MB, reserved on every GPU that loads the library until the
+ * process exits.  Limits: n <= 2097152 particles and n_cells <= 524288
+ * cells per call, else SDM_EINVAL (message in sdm_last_error(NULL)).
+ * The first call on a device resolves the array's device address on that
+ * device (it must be the current device); make that first call before any
+ * stream capture.  The work is only enqueued on stream: nothing is
+ * synchronised.  All calls share the one array, so calls whose work overlaps
+ * on the GPU (other streams, other host threads) race; order them on one
+ * stream.  Cell indices out of range are skipped, not written: then
+ * offsets[n_cells] < n. */
+sdm_status sdm_cell_sort_noalloc(const uint32_t *cell, int64_t n, int32_t n_cells, uint32_t *perm,
+                                 uint32_t *offsets, void *stream);
+
 /* Counters (completes the stream first). */
 sdm_status sdm_get_stats(sdm_ctx *ctx, sdm_stats *out);
 

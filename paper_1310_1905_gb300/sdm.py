@@ -80,7 +80,7 @@ class sdm_timing(C.Structure):
 SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_step_async", "sdm_wait",
            "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
-           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort"]
+           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc"]
 
 
 def lib_path() -> str:
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
     L.sdm_timing_enable.argtypes = [ctx, C.c_int]
     L.sdm_get_timing.argtypes = [ctx, P(sdm_timing), C.c_int]
     L.sdm_cell_sort.argtypes = [V, I64, C.c_int32, V, V, V]
+    L.sdm_cell_sort_noalloc.argtypes = [V, I64, C.c_int32, V, V, V]
     for s in SYMBOLS:
         if s != "sdm_last_error":
             getattr(L, s).restype = C.c_int
@@ -316,6 +317,17 @@ def sdm_cell_sort(cell, n_cells: int, perm, offsets, stream=None):
                          C.c_void_p(offsets.data_ptr()), C.c_void_p(stream or 0))
     if st != 0:
         raise SdmError(st, "sdm_cell_sort failed")
+
+
+def sdm_cell_sort_noalloc(cell, n_cells: int, perm, offsets, stream=None):
+    """The allocation-free variant (fixed device scratch, enqueue only)."""
+    L = load()
+    st = L.sdm_cell_sort_noalloc(C.c_void_p(cell.data_ptr()), cell.numel(), n_cells,
+                                 C.c_void_p(perm.data_ptr()), C.c_void_p(offsets.data_ptr()),
+                                 C.c_void_p(stream or 0))
+    if st != 0:
+        msg = L.sdm_last_error(None)
+        raise SdmError(st, msg.decode() if msg else "")
 
 
 # ---------------------------------------------------------------- object wrapper
