@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="icmw_2d", choices=["icmw_2d", "updraft_3d", "golovin_box"])
+    ap.add_argument("--workload", default="icmw_2d", choices=["icmw_2d", "updraft_3d", "golovin_box", "ensemble", "serve"])
+    ap.add_argument("--members", type=int, default=256)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -202,6 +203,106 @@ def run_gpu(args, rank: int, world: int):
     return res
 
 
+def run_ensemble(args, rank: int, world: int) -> dict:
+    """Batched ensemble (256 ragged 0D members, mixed precision by default):
+    one graph-captured step for all members, against the same members
+    stepped one after another as single-member solves."""
+    import torch
+
+    from paper_1310_1905_gb300.ensemble import Ensemble
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    members = workloads.ensemble_members(args.members, seed=rank)
+    opts = dict(adve=0, sedi=0, cond=1, coal=1, RH_max=44.0, sstp_cond=10, sstp_coal=10)
+    n_sd = sum(m["n_sd"] for m in members)
+    prec = args.precision if args.precision != "fp64" else "mixed"
+    ens = Ensemble(precision=prec, max_sd=n_sd + 1024, max_members=len(members))
+    ids = [ens.add(m) for m in members]
+    tile, thr = ens.autotune(opts)
+    ens.use_graph(True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    t = [0.0]
+
+    def step(e, idmap):
+        r = workloads.parcel_rhod(members, t[0] + 1.0)
+        e.step(opts, rhod={idmap[k]: v for k, v in r.items() if k in idmap})
+        e.wait()
+
+    idmap = dict(enumerate(ids))
+    for _ in range(args.warmup):
+        step(ens, idmap)
+        t[0] += 1.0
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    clocks.start()
+    t_tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(ens, idmap)
+        t_tot += time.perf_counter() - t0
+        t[0] += 1.0
+    clk = clocks.stop()
+    stats = ens.stats()
+    ens.close()
+    # sequential plain solves: every member its own one-member ensemble
+    solo = []
+    for k, m in enumerate(members):
+        e = Ensemble(precision=prec, max_sd=m["n_sd"], max_members=1)
+        solo.append((e, {k: e.add(m)}))
+    seq_steps = max(1, min(3, args.steps))
+    for e, im in solo:
+        step(e, im)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(seq_steps):
+        for e, im in solo:
+            step(e, im)
+    t_seq = time.perf_counter() - t0
+    for e, _ in solo:
+        e.close()
+    return dict(t=dist_max(t_tot, world), n_sd=n_sd, steps=args.steps, clocks=clk, tile=(tile, thr),
+                seq_value=n_sd * seq_steps / t_seq, stats=stats, precision=prec, members=len(members))
+
+
+def run_serve(args, rank: int) -> dict:
+    """Served stream: Poisson arrivals of parcel/box requests, N_sd
+    log-uniform in [1e3, 2e6], w in [0.1, 5] m/s, mixed precision.  A fixed
+    window of requests with the step counts of the served workload scaled by
+    1/10 (30-180 steps) so that a run takes seconds; served at the offered
+    rate (200 req/s, above capacity) and at half the measured capacity."""
+    import torch
+
+    from paper_1310_1905_gb300.serve import Server, poisson_requests
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.5)
+
+    def rhod_fn(m, t):
+        return float(workloads.hydrostatic_rhod(np.array([m["z0"] + m["w"] * t]), 289.0, 7.5e-3, 101500.0)[0])
+
+    n_req = max(8, args.steps * 2)
+    members = workloads.ensemble_members(n_req, seed=100 + rank, n_min=1e3, n_max=2e6, parcel_fraction=0.8)
+    out = {}
+    cap = None
+    for label, rate in (("offered_200_per_s", 200.0), ("half_capacity", None)):
+        if rate is None:
+            mean_work = np.mean([m["n_sd"] for m in members]) * 105.0
+            rate = 0.5 * cap / mean_work
+        reqs = poisson_requests(members, rate, (30, 180), seed=7, rhod_fn=rhod_fn)
+        srv = Server(mem_budget_bytes=budget, precision=args.precision if args.precision != "fp64" else "mixed")
+        st = srv.run(reqs)
+        srv.close()
+        st["rate_per_s"] = rate
+        out[label] = st
+        if cap is None:
+            cap = st["sd_steps_per_s"]
+    return dict(out=out, n_req=n_req, budget=budget)
+
+
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -273,6 +374,44 @@ def main():
             dist.destroy_process_group()
         return
 
+    if args.workload == "serve":
+        r = run_serve(args, rank)
+        if rank == 0:
+            sat = r["out"]["offered_200_per_s"]
+            line = dict(metric=METRIC, value=sat["sd_steps_per_s"], unit=UNIT, n_gpus=world, steps=args.steps,
+                        warmup=0, ms_per_step=sat["wall_s"] / max(1, sat["steps"]) * 1e3, higher_is_better=True,
+                        scaling="weak", vs_baseline=None, dtype="f64/f32", data="synthetic",
+                        config=dict(workload=f"served stream: {r['n_req']} Poisson requests, parcel/box, N_sd "
+                                             f"log-uniform in [1e3, 2e6], 30-180 steps, mixed precision, "
+                                             f"arena {r['budget'] / 1e9:.1f} GB"),
+                        latency={k: dict(p50_s=v["p50_latency_s"], p99_s=v["p99_latency_s"],
+                                         rate_per_s=v["rate_per_s"], sd_steps_per_s=v["sd_steps_per_s"],
+                                         mean_queue_wait_s=v["mean_queue_wait_s"], served=v["served"])
+                                 for k, v in r["out"].items()},
+                        timing="host wall clock over the whole window")
+            print(json.dumps(line), flush=True)
+        return
+    if args.workload == "ensemble":
+        r = run_ensemble(args, rank, world)
+        if rank == 0:
+            v = r["n_sd"] * r["steps"] * world / r["t"]
+            line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                        ms_per_step=r["t"] / args.steps * 1e3, higher_is_better=True, scaling="weak",
+                        vs_baseline=None, dtype="f64/f32" if r["precision"] == "mixed" else "f64",
+                        data="synthetic",
+                        config=dict(workload=f"ensemble: {r['members']} ragged 0D box/parcel members, N_sd "
+                                             f"log-uniform in [1e3, 1e6] ({r['n_sd']} SDs), {r['precision']} "
+                                             f"precision, graph-captured step, autotuned tile {r['tile']}",
+                                    n_sd=r["n_sd"], l2="flushed before every timed step"),
+                        clocks=r["clocks"], timing="host wall clock around step + wait (graph replay)",
+                        sequential=dict(value=r["seq_value"], unit=UNIT,
+                                        how="the same members, one single-member solve after another"),
+                        speedup_vs_sequential=v / r["seq_value"])
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     res = run_gpu(args, rank, world)
     if rank != 0:
         if world > 1:

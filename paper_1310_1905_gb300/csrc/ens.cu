@@ -151,7 +151,7 @@ __global__ void k_ens_init(SdArrays s, uint32_t *mem, const MemberDev *M, const 
 
 __global__ void k_ens_rhod(MemberDev *M, const double *rhod, int nm) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= nm) return;
+    if (m >= nm || rhod[m] == M[m].rhod) return;
     M[m].rhod = rhod[m];
     M[m].dV = M[m].md / rhod[m];
 }
@@ -331,7 +331,9 @@ __global__ void k_ens_pairs(SdArrays s, const MemberDev *M, const uint32_t *aux,
             const unsigned long long Nmax = Na > Nb ? Na : Nb;
             double P;
             bool acc_ok;
-            const Thermo t = thermo_eval(md.th, md.rv, md.rhod, 44.0);
+            struct {
+                double nu, cX;
+            } t{md.nu, md.cX};
             if (p.mixed) {
                 float K;
                 if (p.kernel == SDM_KERNEL_GOLOVIN) {
@@ -386,6 +388,16 @@ __global__ void k_ens_pairs(SdArrays s, const MemberDev *M, const uint32_t *aux,
         if (a3) atomicAdd(&st->n_pgt1, (unsigned long long)a3);
         if (mp > 0.0) atomicMax(&st->max_p_bits, (unsigned long long)__double_as_longlong(mp));
     }
+}
+
+// air viscosity and Best-number factor of each member for this step's
+// terminal velocities (from theta, r_v, rho_d after condensation)
+__global__ void k_ens_ambient(MemberDev *M, int nm) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nm) return;
+    const Thermo t = thermo_eval(M[m].th, M[m].rv, M[m].rhod, 44.0);
+    M[m].nu = t.nu;
+    M[m].cX = t.cX;
 }
 
 __global__ void k_ens_step_done(MemberDev *M, int nm) {
@@ -578,6 +590,7 @@ sdm_status enqueue_step(sdm_ens *e, const sdm_opts &o) {
     if (o.coal) {
         EnsCoalParams p{e->eo.dt, o.sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b};
         const int kb = mixed ? 4 : 8, ab = aux_bytes_for(nm);
+        k_ens_ambient<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
         for (int sub = 0; sub < o.sstp_coal; ++sub) {
             k_ens_active<<<nm, 256, 0, st>>>(e->s[e->cur], e->mdev);
             k_ens_keys<<<grid_for(e->n_sd, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, e->n_sd,

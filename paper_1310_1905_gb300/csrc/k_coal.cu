@@ -27,7 +27,6 @@ struct CoalParams {
     uint64_t seed, step;
 };
 
-constexpr int kWarpCap = 64;
 constexpr int kWarpsPerBlock = 4;
 
 struct KeyRec {
@@ -45,32 +44,43 @@ __device__ __forceinline__ KeyRec shfl_rec(const KeyRec &r, int src) {
     return o;
 }
 
-// bitonic sort of 64 records, lane l holding positions 2l (a) and 2l+1 (b)
-__device__ __forceinline__ void warp_sort64(KeyRec &a, KeyRec &b, int lane) {
+// bitonic sort of 32 R records, lane l holding positions R l .. R l + R - 1:
+// exchanges across distance j < R stay in registers, longer ones go
+// through shuffles with lane l ^ (j / R)
+template <int R>
+__device__ __forceinline__ void warp_sort(KeyRec (&v)[R], int lane) {
 #pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-        const bool up = ((2 * lane) & k) == 0;
+    for (int k = 2; k <= 32 * R; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 1) {
-                const bool sw = up ? rec_less(b, a) : rec_less(a, b);
-                if (sw) {
-                    const KeyRec t = a;
-                    a = b;
-                    b = t;
+            if (j < R) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int rp = r ^ j;
+                    if (rp > r) {
+                        const bool up = ((R * lane + r) & k) == 0;
+                        const bool sw = up ? rec_less(v[rp], v[r]) : rec_less(v[r], v[rp]);
+                        if (sw) {
+                            const KeyRec t = v[r];
+                            v[r] = v[rp];
+                            v[rp] = t;
+                        }
+                    }
                 }
             } else {
-                const int pl = lane ^ (j >> 1);
-                const KeyRec pa = shfl_rec(a, pl), pb = shfl_rec(b, pl);
-                const bool lower = (lane & (j >> 1)) == 0;
-                const bool keep_min = (up == lower);
-                const bool a_lt = rec_less(a, pa), b_lt = rec_less(b, pb);
-                if (keep_min) {
-                    if (!a_lt) a = pa;
-                    if (!b_lt) b = pb;
-                } else {
-                    if (a_lt) a = pa;
-                    if (b_lt) b = pb;
+                const int d = j / R;
+                const int pl = lane ^ d;
+                const bool lower = (lane & d) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const bool up = ((R * lane + r) & k) == 0;
+                    const KeyRec o = shfl_rec(v[r], pl);
+                    const bool lt = rec_less(v[r], o);
+                    if (up == lower) {
+                        if (!lt) v[r] = o;
+                    } else {
+                        if (lt) v[r] = o;
+                    }
                 }
             }
         }
@@ -146,14 +156,16 @@ __device__ __forceinline__ int collide(Acc &A, int a, int b) {
 }
 
 // ---------------------------------------------------------------- warp path
+template <int CAP>
 struct WarpSmem {
-    unsigned long long N[kWarpCap], acc[kWarpCap];
-    double rw2[kWarpCap], rd3[kWarpCap], kappa[kWarpCap], vt[kWarpCap];
-    uint32_t uid[kWarpCap];
+    unsigned long long N[CAP], acc[CAP];
+    double rw2[CAP], rd3[CAP], kappa[CAP], vt[CAP];
+    uint32_t uid[CAP];
 };
 
+template <int CAP>
 struct SmemAcc {
-    WarpSmem *w;
+    WarpSmem<CAP> *w;
     __device__ unsigned long long N(int i) const { return w->N[i]; }
     __device__ double rw2(int i) const { return w->rw2[i]; }
     __device__ double rd3(int i) const { return w->rd3[i]; }
@@ -164,39 +176,43 @@ struct SmemAcc {
     __device__ void setkappa(int i, double v) { w->kappa[i] = v; }
 };
 
+// cells of up to 32 R super-droplets, one warp each, R per lane
+template <int R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_coal_warp(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
                 const double *amb, CoalParams p, uint32_t *bigcells, DevStats *st) {
-    __shared__ WarpSmem sm[kWarpsPerBlock];
+    constexpr int CAP = 32 * R;
+    __shared__ WarpSmem<CAP> sm[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int c = blockIdx.x * kWarpsPerBlock + wib;
     if (c >= p.g.n_cells) return;
-    WarpSmem &W = sm[wib];
+    WarpSmem<CAP> &W = sm[wib];
     const uint32_t beg = offset[c];
     const int n = (int)(offset[c + 1] - beg);
-    if (n > kWarpCap) {
+    if (n > CAP) {
         if (lane == 0) bigcells[atomicAdd(&st->n_big, 1u)] = (uint32_t)c;
         return;
     }
     // gather and order by id
-    KeyRec r0{0, ~0ull}, r1{0, ~0ull};
-    if (2 * lane < n) {
-        const uint32_t pi = perm[beg + 2 * lane];
-        r0.pk = ((unsigned long long)src.uid[pi] << 32) | pi;
+    KeyRec v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int q = R * lane + r;
+        v[r] = KeyRec{0, ~0ull};
+        if (q < n) {
+            const uint32_t pi = perm[beg + q];
+            v[r].pk = ((unsigned long long)src.uid[pi] << 32) | pi;
+        }
     }
-    if (2 * lane + 1 < n) {
-        const uint32_t pi = perm[beg + 2 * lane + 1];
-        r1.pk = ((unsigned long long)src.uid[pi] << 32) | pi;
-    }
-    warp_sort64(r0, r1, lane);
+    warp_sort<R>(v, lane);
     const double nu = amb[2 * c], cX = amb[2 * c + 1];
     const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int q = 2 * lane + r;
+    for (int r = 0; r < R; ++r) {
+        const int q = R * lane + r;
         if (q < n) {
-            const uint32_t pi = (uint32_t)((r ? r1 : r0).pk & 0xffffffffu);
-            const uint32_t id = (uint32_t)((r ? r1 : r0).pk >> 32);
+            const uint32_t pi = (uint32_t)(v[r].pk & 0xffffffffu);
+            const uint32_t id = (uint32_t)(v[r].pk >> 32);
             W.N[q] = src.N[pi];
             W.rw2[q] = src.rw2[pi];
             W.rd3[q] = src.rd3[pi];
@@ -213,43 +229,55 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     unsigned long long n_pairs = 0, n_coll = 0, n_pgt1 = 0;
     double max_p = 0.0;
     if (p.coal && n >= 2) {
-        SmemAcc A{&W};
+        SmemAcc<CAP> A{&W};
         const double dtpp = p.g.dt / p.sstp;
         for (int sub = 0; sub < p.sstp; ++sub) {
-            KeyRec k0{~0ull, ~0ull}, k1{~0ull, ~0ull};
-            bool act0 = false, act1 = false;
+            int my_act = 0;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int q = 2 * lane + r;
+            for (int r = 0; r < R; ++r) {
+                const int q = R * lane + r;
+                v[r] = KeyRec{~0ull, ~0ull};
                 if (q < n && W.N[q] > 0) {
                     const u64x4 w = philox4x64(W.uid[q], (uint64_t)sub, p.step, kStreamCoal, p.seed, 0);
                     W.acc[q] = w.v[1];
-                    KeyRec kr{key_of(p, w.v[0]), ((unsigned long long)W.uid[q] << 32) | (unsigned)q};
-                    if (r) {
-                        k1 = kr;
-                        act1 = true;
-                    } else {
-                        k0 = kr;
-                        act0 = true;
-                    }
+                    v[r] = KeyRec{key_of(p, w.v[0]), ((unsigned long long)W.uid[q] << 32) | (unsigned)q};
+                    my_act++;
                 }
             }
-            const int m = __popc(__ballot_sync(0xffffffffu, act0)) + __popc(__ballot_sync(0xffffffffu, act1));
+            const int m = __reduce_add_sync(0xffffffffu, (unsigned)my_act);
             __syncwarp();
             if (m < 2) continue;
-            warp_sort64(k0, k1, lane);
+            warp_sort<R>(v, lane);
             const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
-            if (2 * lane + 1 < m) {
-                const int a = (int)(k0.pk & 0xffu), b = (int)(k1.pk & 0xffu);
-                const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
-                const double P = prob(p, Nmax, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b], dtpp, scale);
-                n_pairs++;
-                if (P > 1.0) n_pgt1++;
-                max_p = fmax(max_p, P);
-                if (accepted(p, W.acc[a], P)) {
-                    const int S = collide(A, a, b);
-                    if (geo) W.vt[S] = vt_of(p, W.rw2[S], nu, cX);
-                    n_coll++;
+            // sorted positions R lane + r; pairs (2k, 2k + 1) are in one lane
+            KeyRec pa[R >= 2 ? R / 2 : 1], pb[R >= 2 ? R / 2 : 1];
+            if constexpr (R >= 2) {
+#pragma unroll
+                for (int r = 0; r < R; r += 2) {
+                    pa[r / 2] = v[r];
+                    pb[r / 2] = v[r + 1];
+                }
+            } else {  // one record per lane: the pair's second half is in lane + 1
+                pa[0] = v[0];
+                pb[0] = shfl_rec(v[0], lane ^ 1);
+            }
+#pragma unroll
+            for (int h = 0; h < (R >= 2 ? R / 2 : 1); ++h) {
+                const KeyRec ka = pa[h], kb = pb[h];
+                const int pos = R >= 2 ? R * lane + 2 * h : lane;
+                const bool mine = R >= 2 || (lane & 1) == 0;
+                if (mine && pos + 1 < m) {
+                    const int a = (int)(ka.pk & 0xffu), b = (int)(kb.pk & 0xffu);
+                    const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
+                    const double P = prob(p, Nmax, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b], dtpp, scale);
+                    n_pairs++;
+                    if (P > 1.0) n_pgt1++;
+                    max_p = fmax(max_p, P);
+                    if (accepted(p, W.acc[a], P)) {
+                        const int S = collide(A, a, b);
+                        if (geo) W.vt[S] = vt_of(p, W.rw2[S], nu, cX);
+                        n_coll++;
+                    }
                 }
             }
             __syncwarp();
@@ -257,8 +285,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     unsigned zeros = 0;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int q = 2 * lane + r;
+    for (int r = 0; r < R; ++r) {
+        const int q = R * lane + r;
         if (q < n) {
             dst.N[beg + q] = W.N[q];
             dst.rw2[beg + q] = W.rw2[q];
@@ -450,8 +478,18 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     if (e == cudaSuccess) e = cudaMemsetAsync(&c->dstats->n_zero, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     const int nb = (c->grid.n_cells + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_coal_warp<<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
-                                                           c->bigcells, c->dstats);
+    // records per lane: cells hold sd_conc on average and spread around it
+    // as super-droplets move, so the warp path covers twice the mean
+    const int per_cell = c->G * c->oi.sd_conc;
+    if (per_cell <= 16)
+        k_coal_warp<1><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
+                                                                  c->bigcells, c->dstats);
+    else if (per_cell <= 32)
+        k_coal_warp<2><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
+                                                                  c->bigcells, c->dstats);
+    else
+        k_coal_warp<4><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
+                                                                  c->bigcells, c->dstats);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(unsigned long long) * 3 * kBigCellCap;

@@ -114,8 +114,51 @@ struct SolveCounters {
     int euler, fallback;
 };
 
+// The growth rate of eq. (maxmason) rearranged for FP64 throughput: with
+// r^-1 computed once, Kn = lambda r^-1, and beta = (1 + Kn)/D(Kn),
+//   D = a / D_M, K = b / D_T,   a = D0 (1 + Kn_M) Sh/2,  b = K0 (1 + Kn_T) Nu/2,
+//   D_eff = D K / (K + Dterm D) = a b / (b D_M + Dterm a D_T),
+//   a_w = num / den,
+// so that g = 2 a b (rho_v den - rho_vs num e^(A/r)) / (rho_w (b D_M + Dterm a D_T) den)
+// takes one division where the term-by-term form takes about ten.  It equals
+// growth() up to rounding.
+SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, int physics) {
+    using namespace phys;
+    const double r = sqrt(x);
+    const double rinv = 1.0 / r;
+    const double r3 = x * r;
+    const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
+    const double kel = exp(t.A * rinv);
+    double a = D0, b = K0, DM = 1.0, DT = 1.0;
+    if (physics) {
+        const double c1 = 4.0 / 3.0 + 0.377, c2 = 4.0 / 3.0;
+        const double KnM = t.lambda_D * rinv, KnT = t.lambda_K * rinv;
+        DM = 1.0 + c1 * KnM + c2 * KnM * KnM;
+        DT = 1.0 + c1 * KnT + c2 * KnT * KnT;
+        const double X = t.cX * r3;
+        const double e = 4.0 / (delta0 * delta0 * sqrt(C0)) * sqrt(X);
+        const double s = e / (sqrt(1.0 + e) + 1.0);
+        const double Re = delta0 * delta0 / 4.0 * s * s;
+        const double fRe = Re > 1.0 ? pow(Re, 0.077) : 1.0;
+        const double Sh = 1.0 + cbrt(1.0 + Re * t.Sc) * fRe;
+        const double Nu = 1.0 + cbrt(1.0 + Re * t.Pr) * fRe;
+        a = D0 * (1.0 + KnM) * Sh * 0.5;
+        b = K0 * (1.0 + KnT) * Nu * 0.5;
+    }
+    return 2.0 * a * b * (t.rho_v_eff * den - t.rho_vs * num * kel) /
+           (rho_w * (b * DM + t.Dterm * a * DT) * den);
+}
+
+SDM_HD double fres_fast(double x, double x0, double rd3, double kappa, const Thermo &t, double dtp,
+                        int physics) {
+    return x - x0 - dtp * growth_fast(x, rd3, kappa, t, physics);
+}
+
 __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
                                  const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
+    // g(x0) with the term-by-term formula: it sets the bracket and, when the
+    // bracket is ill-posed, the result itself, where its rounding is not
+    // damped by the stiffness of the implicit equation
     const double g0 = growth(x0, rd3, kappa, t, physics);
     const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
@@ -134,7 +177,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         return false;
     };
     auto positive64 = [&](double x) -> bool {
-        return fres(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
+        return fres_fast(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
     };
     bool ok;
     bool pa = positive(a, &ok);
@@ -164,17 +207,19 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     }
     if (!polish) return 0.5 * (lo + hi);
     // FP64 polish inside [lo, hi], keeping the bracket with exact signs
-    double xk = mid, fk = fres(xk, x0, rd3, kappa, t, dtp, physics);
+    double xk = mid, fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
     double xp = 0.0, fp = 0.0;
     bool have_prev = false;
     for (int k = 0; k < 12; ++k) {
         if (fk == 0.0) return xk;
         if ((fk > 0.0) == plo) lo = xk;
         else hi = xk;
-        if (hi - lo <= 0x1p-48 * hi) return 0.5 * (lo + hi);
+        if (hi - lo <= 0x1p-46 * hi) return 0.5 * (lo + hi);
         double xn;
+        bool secant = false;
         if (have_prev && fk != fp) {
-            xn = xk - fk * (xk - xp) / (fk - fp);  // secant
+            xn = xk - fk * (xk - xp) / (fk - fp);
+            secant = true;
         } else {
             float eg, dg;
             growth_f((float)xk, rd3f, kf, tf, physics, &eg, &dg);
@@ -182,14 +227,25 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
             xn = fpr != 0.0 ? xk - fk / fpr : 0.5 * (lo + hi);
         }
         // a step past an end of the bracket says the root hugs that end
-        if (!(xn < hi)) xn = hi - (hi - lo) * 0.015625;
-        if (!(xn > lo)) xn = lo + (hi - lo) * 0.015625;
-        if (fabs(xn - xk) <= 0x1p-50 * xk) return xn;
+        bool clamped = false;
+        if (!(xn < hi)) {
+            xn = hi - (hi - lo) * 0.015625;
+            clamped = true;
+        }
+        if (!(xn > lo)) {
+            xn = lo + (hi - lo) * 0.015625;
+            clamped = true;
+        }
+        // the secant converges superlinearly: once its step is below 2^-30 x
+        // the error left is of order (2^-30)(previous step) x, far below
+        // 2^-46 x; a Newton step with the approximate FP32 derivative must
+        // itself be that small
+        if (!clamped && fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk) return xn;
         xp = xk;
         fp = fk;
         have_prev = true;
         xk = xn;
-        fk = fres(xk, x0, rd3, kappa, t, dtp, physics);
+        fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
     }
     // did not settle: finish with the exact bisection in the current bracket
     cnt.fallback++;
@@ -214,7 +270,8 @@ __host__ __device__ bool solve_rw2_f32(double x0, double rd3, double kappa, cons
     const float rd3f = (float)rd3, kf = (float)kappa;
     float eg, dg;
     const float g0 = growth_f((float)x0, rd3f, kf, tf, physics, &eg, nullptr);
-    const float lo_d = fmaxf((float)(rd2_of(rd3) - x0), fminf(2.0f * dtp * g0, 0.0f));
+    const float rdf = cbrtf(rd3f);
+    const float lo_d = fmaxf((float)((double)(rdf * rdf) - x0), fminf(2.0f * dtp * g0, 0.0f));
     const float hi_d = fmaxf(2.0f * dtp * g0, 0.0f);
     auto f = [&](float d, float *der) -> float {
         const float g = growth_f((float)(x0 + (double)d), rd3f, kf, tf, physics, &eg, der ? &dg : nullptr);
@@ -240,7 +297,9 @@ __host__ __device__ bool solve_rw2_f32(double x0, double rd3, double kappa, cons
         if (!(dn > lo && dn < hi)) dn = 0.5f * (lo + hi);
         const float step = fabsf(dn - d);
         d = dn;
-        if (step <= 1e-6f * fmaxf(fabsf(d), 1e-30f) || hi - lo <= 1e-6f * fmaxf(fabsf(hi), fabsf(lo))) {
+        // settled to FP32 resolution of r_w^2 itself (not of the increment)
+        const float tol = 2.4e-7f * (float)x0;
+        if (step <= tol || hi - lo <= tol) {
             *x1 = x0 + (double)d;
             return true;
         }

@@ -280,6 +280,7 @@ struct MemberDev {
     uint32_t zeros;
     double dV, md;           // volume [m^3], dry-air mass [kg]
     double th, rv, rhod;
+    double nu, cX;           // air viscosity and Best-number factor for v_t
     unsigned long long seed, step;
 };
 

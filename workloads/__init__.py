@@ -148,3 +148,39 @@ def updraft_3d(nx: int = 128, ny: int = 128, nz: int = 128, sd_conc: int = 32, s
                seed=seed, physics=physics)
     return Workload("updraft_3d", cfg, th, rv, rhod, rhoCx, rhoCy, np.ascontiguousarray(rhoCz),
                     dict(OPTS_DEFAULT), n_steps)
+
+
+def ensemble_members(n_members: int = 256, seed: int = 0, n_min: float = 1e3, n_max: float = 1e6,
+                     parcel_fraction: float = 0.5) -> list[dict]:
+    """Ragged ensemble of 0D members: N_sd log-uniform in [n_min, n_max];
+    one or two lognormal modes sharing one kappa, with log-uniform mode radius
+    (0.02-0.1 um) and concentration (50-500 cm^-3), sigma in [1.3, 1.8],
+    kappa in [0.2, 1.2]; boxes and adiabatic parcels (updraft w in
+    [0.1, 5] m/s from 600 m in the 2D case's hydrostatic column).  Each member
+    is a dict for the ensemble binding plus 'w' and 'z0' for parcels."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_members):
+        n_sd = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        kappa = float(rng.uniform(0.2, 1.2))
+        modes = []
+        for _ in range(int(rng.integers(1, 3))):
+            modes.append(dict(rm=float(math.exp(rng.uniform(math.log(0.02e-6), math.log(0.1e-6)))),
+                              sigma=float(rng.uniform(1.3, 1.8)),
+                              n_stp=float(math.exp(rng.uniform(math.log(50e6), math.log(500e6)))), kappa=kappa))
+        parcel = bool(rng.uniform() < parcel_fraction)
+        z0 = 600.0
+        rhod0 = float(hydrostatic_rhod(np.array([z0]), 289.0, 7.5e-3, 101500.0)[0])
+        out.append(dict(n_sd=n_sd, dV=1.0, th=289.0, rv=7.5e-3, rhod=rhod0, modes=modes,
+                        seed=int(seed) * 100003 + k, w=float(rng.uniform(0.1, 5.0)) if parcel else 0.0, z0=z0))
+    return out
+
+
+def parcel_rhod(members: list[dict], t: float) -> dict:
+    """rho_d at time t of every parcel member (index -> value), rising at w
+    from z0 through the 2D case's hydrostatic column."""
+    out = {}
+    for k, m in enumerate(members):
+        if m.get("w", 0.0) > 0.0:
+            out[k] = float(hydrostatic_rhod(np.array([m["z0"] + m["w"] * t]), 289.0, 7.5e-3, 101500.0)[0])
+    return out
