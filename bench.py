@@ -40,6 +40,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (4 FP64 flops) per SM per clock
 FP64_FLOPS_PER_SM_CLK = 4.0
 N_SM = 152
+# ncu, k_condense on the 2D case (profiles/k_condense_icmw_2d_fp64.md)
+COND_FP64_FLOPS_PER_SD_SUBSTEP = 1381.0
+COND_DRAM_BYTES_PER_LAUNCH = 11.87e6
 
 
 def parse():
@@ -423,20 +426,23 @@ def main():
     value = total_sd_steps / res["t_dev"]
     tim = res["timing"]
     pk = peaks()
-    # dominant kernel: condensation, FP64-arithmetic bound
+    # dominant kernel: condensation, bound by FP64 arithmetic.  Its FP64 work
+    # per SD-substep (2 DFMA + DADD + DMUL thread instructions) is measured
+    # with ncu on this workload (profiles/k_condense_icmw_2d_fp64.md); the
+    # bench multiplies it by the SD-substeps of one launch and divides by the
+    # launch's CUDA-event time.
     cond_ms = tim["cond_ms"] / max(1, tim["cond_launches"])
     clk = res["clocks"]
     sm_mhz = clk.get("sm_mhz") or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
     fp64_peak = FP64_FLOPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
-    flops_per_sd_substep = float(os.environ.get("SDM_COND_FLOPS_PER_SD_SUBSTEP", "0") or 0)
-    roof = None
-    if flops_per_sd_substep > 0:
-        achieved = flops_per_sd_substep * res["n_sd"] * w.opts["sstp_cond"] / (cond_ms * 1e-3) / 1e12
+    units = res["n_sd"] * w.opts["sstp_cond"]
+    if args.precision == "fp64" and args.workload == "icmw_2d":
+        achieved = COND_FP64_FLOPS_PER_SD_SUBSTEP * units / (cond_ms * 1e-3) / 1e12
         roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
-                    frac=achieved / fp64_peak, traffic=None,
-                    peak_source="FP64 2 DFMA/SM/clk x 152 SMs at the sampled SM clock (derived)")
+                    frac=achieved / fp64_peak, traffic=COND_DRAM_BYTES_PER_LAUNCH,
+                    flops_per_sd_substep=COND_FP64_FLOPS_PER_SD_SUBSTEP,
+                    peak_source="derived: 4 FP64 flop/SM/clk x 152 SMs x sampled SM clock (1.25 TFLOP/s nominal)")
     else:
-        # condensation bytes per SD-step over the kernel time, against HBM
         bytes_per_launch = 40.0 * res["n_sd"]
         achieved = bytes_per_launch / (cond_ms * 1e-3) / 1e9
         hbm = pk.get("hbm_gbs", 6800.0)
