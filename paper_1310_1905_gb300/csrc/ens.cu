@@ -71,6 +71,7 @@ struct sdm_ens {
     uint32_t *val[2] = {nullptr, nullptr}, *aux[2] = {nullptr, nullptr};
     uint32_t *hist = nullptr, *scan_tmp = nullptr;
     unsigned long long *acc = nullptr;
+    uint32_t *live = nullptr;  // live super-droplets per member (coalescence substep)
     double *rhod_dev = nullptr, *rhod_pin = nullptr;
     double *outbuf = nullptr;
     sdm::DevStats *dstats = nullptr, *hstats = nullptr;
@@ -163,6 +164,8 @@ constexpr int kEnsRecyclePerStep = 64;
 
 __global__ void k_ens_recycle(SdArrays s, MemberDev *M, DevStats *st) {
     const MemberDev &md = M[blockIdx.x];
+    // the coalescence kernel counts every multiplicity that reaches zero
+    if (md.zeros == 0) return;
     __shared__ unsigned s_z;
     __shared__ unsigned long long s_best;
     __shared__ uint32_t s_bestq;
@@ -177,7 +180,11 @@ __global__ void k_ens_recycle(SdArrays s, MemberDev *M, DevStats *st) {
     zc = __reduce_add_sync(0xffffffffu, zc);
     if ((threadIdx.x & 31) == 0 && zc) atomicAdd(&s_z, zc);
     __syncthreads();
-    if (s_z == 0) return;
+    const unsigned total = s_z;
+    if (total == 0) {
+        if (threadIdx.x == 0) M[blockIdx.x].zeros = 0;
+        return;
+    }
     // the first zeros in storage (= id) order, found by one warp in sequence
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -258,16 +265,24 @@ __global__ void k_ens_recycle(SdArrays s, MemberDev *M, DevStats *st) {
         s.N[z] = Nd / 2;
         s.N[d] = Nd - Nd / 2;
     }
-    if (threadIdx.x == 0 && np) atomicAdd(&st->n_recycled, (unsigned long long)np);
+    if (threadIdx.x == 0) {
+        M[blockIdx.x].zeros = total - np;
+        if (np) atomicAdd(&st->n_recycled, (unsigned long long)np);
+    }
 }
 
+// one warp per member: lane l adds tiles l, l + 32, ... and the warp
+// combines the lanes in a fixed tree (the same order in any ensemble)
 __global__ void k_ens_cond_update(MemberDev *M, const double *tile_sum, int nm, EnsCondParams p,
                                   DevStats *st) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= nm) return;
-    MemberDev &md = M[m];
+    const int64_t m64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (m64 >= nm) return;  // whole warps leave together
+    MemberDev &md = M[m64];
     double sum = 0.0;
-    for (uint32_t t = 0; t < md.ntiles; ++t) sum += tile_sum[md.tile0 + t];
+    for (uint32_t t = lane; t < md.ntiles; t += 32) sum += tile_sum[md.tile0 + t];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane) return;
     const Thermo t = thermo_eval(md.th, md.rv, md.rhod, p.RH_max);
     const double drv = -4.0 * phys::pi * phys::rho_w / (3.0 * md.dV * md.rhod) * sum;
     md.rv = t.rv + drv;
@@ -281,39 +296,50 @@ struct EnsCoalParams {
     double golovin_b;
 };
 
-__global__ void k_ens_active(const SdArrays s, MemberDev *M) {
-    const MemberDev &md = M[blockIdx.x];
-    unsigned cnt = 0;
-    for (uint32_t q = threadIdx.x; q < md.n; q += blockDim.x) cnt += s.N[md.off + q] > 0;
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    __shared__ unsigned tot;
-    if (threadIdx.x == 0) tot = 0;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicAdd(&tot, cnt);
-    __syncthreads();
-    if (threadIdx.x == 0) M[blockIdx.x].active = tot;
-}
-
+// sort keys of one coalescence substep: word 0 of the pairing draw (its
+// 31 leading bits in mixed precision, so that the inactive key 0xFFFFFFFF
+// sorts strictly after every live one); the live super-droplets of each
+// member are counted on the way (block-aggregated atomics: members are
+// stored contiguously, so a block rarely spans more than one)
+template <class K>
 __global__ void k_ens_keys(const SdArrays s, const uint32_t *mem, const MemberDev *M, int64_t n, int sub,
-                           int mixed, unsigned long long *key, uint32_t *val, uint32_t *aux,
-                           unsigned long long *acc) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const uint32_t m = mem[q];
-    const MemberDev &md = M[m];
-    unsigned long long k = ~0ull;
-    if (s.N[q] > 0) {
-        const u64x4 w = philox4x64(s.uid[q], (uint64_t)sub, md.step, kStreamCoal, md.seed, 0);
-        k = mixed ? (w.v[0] >> 32) : w.v[0];
-        acc[q] = w.v[1];
+                           K *key, uint32_t *val, uint32_t *aux, unsigned long long *acc, uint32_t *act) {
+    __shared__ uint32_t s_cnt;
+    const int64_t q0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t q = q0 + threadIdx.x;
+    const bool ok = q < n;
+    const uint32_t m0 = mem[q0];
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    uint32_t m = 0xffffffffu;
+    bool live = false;
+    if (ok) {
+        m = mem[q];
+        const MemberDev &md = M[m];
+        K k = (K)~0ull;
+        if (s.N[q] > 0) {
+            const u64x4 w = philox4x64(s.uid[q], (uint64_t)sub, md.step, kStreamCoal, md.seed, 0);
+            k = sizeof(K) == 4 ? (K)(w.v[0] >> 33) : (K)w.v[0];
+            acc[q] = w.v[1];
+            live = true;
+        }
+        key[q] = k;
+        val[q] = (uint32_t)q;
+        aux[q] = m;
     }
-    key[q] = k;
-    val[q] = (uint32_t)q;
-    aux[q] = m;
+    const unsigned peers = __match_any_sync(0xffffffffu, m);
+    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, live) & peers);
+    if (ok && cnt && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) {
+        if (m == m0) atomicAdd(&s_cnt, cnt);
+        else atomicAdd(&act[m], cnt);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(&act[m0], s_cnt);
 }
 
-__global__ void k_ens_pairs(SdArrays s, const MemberDev *M, const uint32_t *aux, const uint32_t *val,
-                            const unsigned long long *acc, int64_t n, EnsCoalParams p, DevStats *st) {
+__global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const uint32_t *val,
+                            const unsigned long long *acc, const uint32_t *live, int64_t n, EnsCoalParams p,
+                            DevStats *st) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long npair = 0, ncoll = 0, ngt1 = 0;
     double mp = 0.0;
@@ -321,7 +347,7 @@ __global__ void k_ens_pairs(SdArrays s, const MemberDev *M, const uint32_t *aux,
         const uint32_t m = aux[q];
         const MemberDev &md = M[m];
         const uint32_t j = (uint32_t)(q - md.off);
-        const uint32_t act = md.active;
+        const uint32_t act = live[m];
         if ((j & 1u) == 0 && j + 1 < act) {
             const uint32_t a = val[q], b = val[q + 1];
             const double scale = (double)act * (double)(act - 1) / (2.0 * (double)(act / 2));
@@ -368,6 +394,7 @@ __global__ void k_ens_pairs(SdArrays s, const MemberDev *M, const uint32_t *aux,
             if (acc_ok) {
                 const uint32_t L = Na >= Nb ? a : b, S = L == a ? b : a;
                 s.N[L] -= s.N[S];
+                if (Na == Nb) atomicAdd(&M[m].zeros, 1u);  // recycled at the next step
                 const double rwS = s.rw2[S], rwL = s.rw2[L];
                 const double r = cbrt(rwS * sqrt(rwS) + rwL * sqrt(rwL));
                 s.rw2[S] = r * r;
@@ -469,12 +496,6 @@ int aux_bytes_for(int nm) { return nm <= 256 ? 1 : (nm <= 65536 ? 2 : 3); }
 int n_members(const sdm_ens *e) { return (int)e->mhost.size(); }
 
 int64_t max_tiles(const sdm_ens *e) { return e->cap_sd / 128 + e->cap_members + 1; }
-
-std::vector<MemberInitDev> g_unused;
-
-struct Host {
-    std::vector<MemberInitDev> minit;  // host copy of the init table (packed order)
-};
 
 // refresh the host mirror of the fields the device evolves
 sdm_status pull_members(sdm_ens *e) {
@@ -584,23 +605,33 @@ sdm_status enqueue_step(sdm_ens *e, const sdm_opts &o) {
             ECK(launch_ens_cond_tiles(e->s[e->cur], e->mdev, e->tile_member, e->tile_beg, e->tile_end,
                                       e->tile_sum, e->n_tiles, e->cond_threads, p, e->dstats, st),
                 "condensation");
-            k_ens_cond_update<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, e->tile_sum, nm, p, e->dstats);
+            k_ens_cond_update<<<grid_for((int64_t)nm * 32, 128), 128, 0, st>>>(e->mdev, e->tile_sum, nm, p,
+                                                                                e->dstats);
         }
     }
     if (o.coal) {
         EnsCoalParams p{e->eo.dt, o.sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b};
-        const int kb = mixed ? 4 : 8, ab = aux_bytes_for(nm);
+        const int ab = aux_bytes_for(nm);
         k_ens_ambient<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
+        const int64_t n = e->n_sd;
         for (int sub = 0; sub < o.sstp_coal; ++sub) {
-            k_ens_active<<<nm, 256, 0, st>>>(e->s[e->cur], e->mdev);
-            k_ens_keys<<<grid_for(e->n_sd, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, e->n_sd,
-                                                                sub, mixed ? 1 : 0, e->key[0], e->val[0],
-                                                                e->aux[0], e->acc);
-            ECK(radix_sort_pairs<unsigned long long>(e->key[0], e->val[0], e->aux[0], e->key[1], e->val[1],
-                                                     e->aux[1], e->n_sd, kb, ab, e->hist, e->scan_tmp, st),
-                "sort");
-            k_ens_pairs<<<grid_for(e->n_sd, e->pair_threads), e->pair_threads, 0, st>>>(
-                e->s[e->cur], e->mdev, e->aux[0], e->val[0], e->acc, e->n_sd, p, e->dstats);
+            ECK(cudaMemsetAsync(e->live, 0, 4 * (size_t)nm, st), "live counts");
+            if (mixed) {
+                uint32_t *k0 = reinterpret_cast<uint32_t *>(e->key[0]), *k1 = reinterpret_cast<uint32_t *>(e->key[1]);
+                k_ens_keys<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, n, sub,
+                                                                      k0, e->val[0], e->aux[0], e->acc, e->live);
+                ECK(radix_sort_pairs<uint32_t>(k0, e->val[0], e->aux[0], k1, e->val[1], e->aux[1], n, 4, ab, e->hist,
+                                               e->scan_tmp, st),
+                    "sort");
+            } else {
+                k_ens_keys<unsigned long long><<<grid_for(n, 256), 256, 0, st>>>(
+                    e->s[e->cur], e->mem[e->cur], e->mdev, n, sub, e->key[0], e->val[0], e->aux[0], e->acc, e->live);
+                ECK(radix_sort_pairs<unsigned long long>(e->key[0], e->val[0], e->aux[0], e->key[1], e->val[1],
+                                                         e->aux[1], n, 8, ab, e->hist, e->scan_tmp, st),
+                    "sort");
+            }
+            k_ens_pairs<<<grid_for(n, e->pair_threads), e->pair_threads, 0, st>>>(
+                e->s[e->cur], e->mdev, e->aux[0], e->val[0], e->acc, e->live, n, p, e->dstats);
         }
     }
     k_ens_step_done<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
@@ -636,6 +667,7 @@ void free_ens(sdm_ens *e) {
     cudaFree(e->hist);
     cudaFree(e->scan_tmp);
     cudaFree(e->acc);
+    cudaFree(e->live);
     cudaFree(e->rhod_dev);
     cudaFree(e->outbuf);
     cudaFree(e->dstats);
@@ -708,6 +740,7 @@ sdm_status sdm_ens_create(const sdm_ens_opts *o, void *stream, sdm_ens **out) {
     A((void **)&e->hist, 4 * (256 * (size_t)tiles_rs + 1));
     A((void **)&e->scan_tmp, 4 * (256 * (size_t)tiles_rs / 1024 + 4));
     A((void **)&e->acc, 8 * n);
+    A((void **)&e->live, 4 * nm);
     A((void **)&e->rhod_dev, 8 * nm);
     A((void **)&e->outbuf, 8 * nm);
     A((void **)&e->dstats, sizeof(DevStats));

@@ -132,8 +132,10 @@ __device__ __forceinline__ bool accepted(const CoalParams &p, uint64_t w, double
     return p.mixed ? u01f(w) < (float)P : u01(w) < P;
 }
 
+// mixed precision sorts on the 31 leading bits of the draw (ties fall back
+// to id order), the key width the batched ensemble sorts on
 __device__ __forceinline__ unsigned long long key_of(const CoalParams &p, uint64_t w0) {
-    return p.mixed ? (w0 & 0xFFFFFFFF00000000ull) : w0;
+    return p.mixed ? (w0 & 0xFFFFFFFE00000000ull) : w0;
 }
 
 // one collision event: the larger-N member (the first on a tie) keeps its

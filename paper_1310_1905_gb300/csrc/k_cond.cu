@@ -40,16 +40,16 @@ __host__ __device__ double solve_rw2_bisect(double x0, double rd3, double kappa,
 }
 
 // ---------------------------------------------------------------------------
-// Bisection-faithful fast solve.  The bracket, the ill-posedness test and the
-// sequence of midpoints are exactly those of solve_rw2_bisect (FP64 interval
-// arithmetic), but the sign of f at a point is first computed in FP32 with
-// an error bound and trusted when |f| exceeds it; only when FP32 cannot tell
-// (the bracket has shrunk to FP32 resolution) is f evaluated in FP64.  From
-// there a bracketed Newton/secant iteration in FP64 converges to the single
-// sign change inside the current bracket, the same point the remaining
-// halvings of the paper's bisection converge to.  Iterates that leave the
-// bracket are replaced by its midpoint; if the iteration does not settle the
-// exact bisection finishes the job.
+// Fast solve, faithful to the bisection.  The bracket and the ill-posedness
+// test are those of solve_rw2_bisect (FP64).  The sign of f at a point is
+// first computed in FP32 with an error bound and trusted where |f| exceeds
+// it.  (1) The bisection runs on the FP32 increment d = x - x0 while FP32
+// decides; (2) where it stops deciding, a bracketed Newton/secant iteration
+// in FP64 converges to a sign change inside the bracket; (3) an FP32 replay
+// of the remaining halvings checks that the bisection leads to that same
+// sign change (near activation there can be several).  If the iteration
+// does not settle or the replay leaves its root, the exact FP64 bisection
+// finishes the job.
 struct ThermoF {
     float rho_vs, rho_v_eff, A, Dterm, lambda_D, lambda_K, Sc, Pr, cX;
 };
@@ -155,76 +155,94 @@ SDM_HD double fres_fast(double x, double x0, double rd3, double kappa, const The
 }
 
 __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
-                                 const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
+                                          const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
     // g(x0) with the term-by-term formula: it sets the bracket and, when the
     // bracket is ill-posed, the result itself, where its rounding is not
     // damped by the stiffness of the implicit equation
     const double g0 = growth(x0, rd3, kappa, t, physics);
     const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
-    const float rd3f = (float)rd3, kf = (float)kappa, dtpf = (float)dtp;
-    // sign of f(x) > 0, exactly as an FP64 evaluation would decide it
-    auto positive = [&](double x, bool *decided) -> bool {
-        *decided = true;
-        if (x == x0) return (x - x0) - dtp * g0 > 0.0;
-        const double d = x - x0;
+    const float rd3f = (float)rd3, kf = (float)kappa, dtpf = (float)dtp, x0f = (float)x0;
+    // sign of f at the point x0 + d (d an FP32 increment) computed in FP32
+    // and trusted where |f| exceeds its error bound: it is then the sign an
+    // FP64 evaluation gives; *noise is that bound
+    auto positive = [&](float d, bool *decided, float *noise) -> bool {
         float eg;
-        const float g = growth_f((float)x, rd3f, kf, tf, physics, &eg, nullptr);
-        const float f = (float)d - dtpf * g;
-        const float e = 2.4e-7f * fabsf((float)d) + 4.0f * dtpf * eg;
-        if (fabsf(f) > e) return f > 0.0f;
-        *decided = false;
-        return false;
-    };
-    auto positive64 = [&](double x) -> bool {
-        return fres_fast(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
+        const float g = growth_f(x0f + d, rd3f, kf, tf, physics, &eg, nullptr);
+        const float f = d - dtpf * g;
+        *noise = 2.4e-7f * fabsf(d) + 4.0f * dtpf * eg;
+        *decided = fabsf(f) > *noise;
+        return f > 0.0f;
     };
     bool ok;
-    bool pa = positive(a, &ok);
-    if (!ok) pa = positive64(a);
-    bool pb = positive(b, &ok);
-    if (!ok) pb = positive64(b);
+    float nz;
+    // at x0 itself f = -dtp g0 exactly
+    auto end_sign = [&](double x) -> bool {
+        if (x == x0) return -dtp * g0 > 0.0;
+        const bool p = positive((float)(x - x0), &ok, &nz);
+        return ok ? p : fres(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
+    };
+    const bool pa = end_sign(a), pb = end_sign(b);
     if (pa == pb) {
         cnt.euler++;
         return 0.5 * (a + b);
     }
-    double lo = a, hi = b;
     const bool plo = pa;
-    double mid = 0.0;
-    bool polish = false;
-    int it = 0;
-    for (; it < 200; ++it) {
-        if (hi - lo <= 0x1p-52 * hi) return 0.5 * (lo + hi);
-        mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) return 0.5 * (lo + hi);
-        const bool pm = positive(mid, &ok);
+    if (b - a <= 0x1p-52 * b) return 0.5 * (a + b);  // the bisection's own first exit
+    // 1. locate: halve the increment's bracket in FP32 while the signs are
+    //    decided (the same halves the FP64 bisection takes, up to FP32
+    //    rounding of the midpoints)
+    float L = (float)(a - x0), H = (float)(b - x0), mu = 0.0f;
+    bool undecided = false;
+    for (int it = 0; it < 64; ++it) {
+        const float m = 0.5f * (L + H);
+        if (!(m > L && m < H)) break;
+        const bool pm = positive(m, &ok, &nz);
         if (!ok) {
-            polish = true;
+            mu = m;
+            undecided = true;
             break;
         }
-        if (pm == plo) lo = mid;
-        else hi = mid;
+        if (pm == plo) L = m;
+        else H = m;
     }
-    if (!polish) return 0.5 * (lo + hi);
-    // FP64 polish inside [lo, hi], keeping the bracket with exact signs
-    double xk = mid, fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
-    double xp = 0.0, fp = 0.0;
-    bool have_prev = false;
-    for (int k = 0; k < 12; ++k) {
-        if (fk == 0.0) return xk;
+    const float Lu = L, Hu = H;
+    if (!undecided) mu = 0.5f * (L + H);
+    // 2. polish in FP64 inside [lo, hi], keeping the bracket with exact signs
+    double lo = x0 + (double)L, hi = x0 + (double)H;
+    if (!(lo >= a)) lo = a;
+    if (!(hi <= b)) hi = b;
+    double xk = x0 + (double)mu;
+    const bool mu_inside = xk > lo && xk < hi;
+    if (!mu_inside) xk = 0.5 * (lo + hi);
+    double fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
+    const bool pmu = fk > 0.0;  // the FP64 sign at mu, needed by the replay
+    double xp = 0.0, fp = 0.0, slope = 1.0, r = 0.0;
+    bool have_prev = false, settled = false;
+    for (int k = 0; k < 12 && !settled; ++k) {
+        if (fk == 0.0) {
+            r = xk;
+            settled = true;
+            break;
+        }
         if ((fk > 0.0) == plo) lo = xk;
         else hi = xk;
-        if (hi - lo <= 0x1p-46 * hi) return 0.5 * (lo + hi);
+        if (hi - lo <= 0x1p-46 * hi) {
+            r = 0.5 * (lo + hi);
+            settled = true;
+            break;
+        }
         double xn;
         bool secant = false;
         if (have_prev && fk != fp) {
-            xn = xk - fk * (xk - xp) / (fk - fp);
+            slope = (fk - fp) / (xk - xp);
+            xn = xk - fk / slope;
             secant = true;
         } else {
             float eg, dg;
             growth_f((float)xk, rd3f, kf, tf, physics, &eg, &dg);
-            const double fpr = 1.0 - dtp * (double)dg;  // approximate f'
-            xn = fpr != 0.0 ? xk - fk / fpr : 0.5 * (lo + hi);
+            slope = 1.0 - dtp * (double)dg;  // approximate f'
+            xn = slope != 0.0 ? xk - fk / slope : 0.5 * (lo + hi);
         }
         // a step past an end of the bracket says the root hugs that end
         bool clamped = false;
@@ -240,20 +258,69 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         // the error left is of order (2^-30)(previous step) x, far below
         // 2^-46 x; a Newton step with the approximate FP32 derivative must
         // itself be that small
-        if (!clamped && fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk) return xn;
+        if (!clamped && fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk) {
+            r = xn;
+            settled = true;
+            break;
+        }
         xp = xk;
         fp = fk;
         have_prev = true;
         xk = xn;
         fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
     }
-    // did not settle: finish with the exact bisection in the current bracket
+    // 3. replay: near activation f need not be monotonic, and a bracket can
+    //    hold several roots.  The polish found the one nearest mu; the
+    //    bisection takes the one its halvings lead to.  Replaying those
+    //    halvings from the bracket where FP32 stopped deciding (in FP32, and
+    //    in FP64 wherever FP32 cannot tell away from r) checks that they lead
+    //    to r; where they leave it, the exact bisection takes over.
+    if (settled && undecided) {
+        // dr carries r - x0 to FP32: points within a few of its ulps are
+        // taken as r itself
+        const float dr = (float)(r - x0);
+        const float dtol = 4.0f * 5.9604645e-8f * fabsf(dr);
+        float RL = Lu, RH = Hu;
+        bool consistent = true;
+        if (mu_inside) {
+            consistent = fabsf(mu - dr) <= dtol || (pmu == plo) == (mu < dr);
+            if (pmu == plo) RL = mu;
+            else RH = mu;
+        }
+        const double sl = fabs(slope);
+        for (int it = 0; it < 64 && consistent; ++it) {
+            const float m = 0.5f * (RL + RH);
+            if (!(m > RL && m < RH) || fabsf(m - dr) <= dtol) break;
+            bool pm = positive(m, &ok, &nz);
+            if (!ok) {
+                // within a few noise widths of r: the halvings close in on r
+                if ((double)fabsf(m - dr) * sl <= 8.0 * (double)nz) break;
+                pm = fres(x0 + (double)m, x0, rd3, kappa, t, dtp, physics) > 0.0;
+            }
+            if (pm != (plo == (m < dr))) {
+                consistent = false;
+                // continue the exact bisection from this halving's bracket
+                if (pm == plo) RL = m;
+                else RH = m;
+                lo = fmax(a, x0 + (double)RL);
+                hi = fmin(b, x0 + (double)RH);
+                break;
+            }
+            if (pm == plo) RL = m;
+            else RH = m;
+        }
+        if (consistent) return r;
+    } else if (settled) {
+        return r;
+    }
+    // did not settle, or the replay left r: the exact bisection in the
+    // current bracket (FP64 signs, as the paper's bisection takes them)
     cnt.fallback++;
-    for (; it < 200; ++it) {
+    for (int it = 0; it < 200; ++it) {
         if (hi - lo <= 0x1p-52 * hi) break;
         const double m = 0.5 * (lo + hi);
         if (!(m > lo && m < hi)) break;
-        if (positive64(m) == plo) lo = m;
+        if ((fres(m, x0, rd3, kappa, t, dtp, physics) > 0.0) == plo) lo = m;
         else hi = m;
     }
     return 0.5 * (lo + hi);
@@ -325,16 +392,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// LPC lanes per cell (a power of two <= 32): each lane solves every LPC-th
+// super-droplet of its cell, the group's lanes share the cell's
+// thermodynamics and sum through shuffles inside the group.  Fewer lanes per
+// cell give each lane more super-droplets, which evens out the solve's
+// data-dependent cost across the warp.
+template <int LPC>
 __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
                            const double *rhod, Grid g, int sstp, double RH_max, int physics,
                            int solver, int mixed, DevStats *st) {
-    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (warp >= g.n_cells) return;
-    const int c = warp;
-    const uint32_t beg = offset[c], end = offset[c + 1];
-    double thc = th[c], rvc = rv[c];
-    const double rd = rhod[c];
+    const int sl = lane % LPC;
+    const int64_t c64 = gt / LPC;
+    const bool live = c64 < g.n_cells;
+    const int c = live ? (int)c64 : 0;
+    const uint32_t beg = live ? offset[c] : 0, end = live ? offset[c + 1] : 0;
+    double thc = live ? th[c] : 289.0, rvc = live ? rv[c] : 0.0;
+    const double rd = live ? rhod[c] : 1.0;
     const double dtp = g.dt / sstp;
     SolveCounters cnt{0, 0};
     bool bad = false;
@@ -342,7 +417,7 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
         const Thermo t = thermo_eval(thc, rvc, rd, RH_max);
         const ThermoF tf = to_float(t);
         double sum = 0.0;
-        for (uint32_t i = beg + lane; i < end; i += 32) {
+        for (uint32_t i = beg + sl; i < end; i += LPC) {
             const unsigned long long N = s.N[i];
             if (N == 0) continue;
             const double x0 = s.rw2[i];
@@ -360,18 +435,21 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
             s.rw2[i] = x1;
             sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
         }
-        sum = warp_sum(sum);
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         const double drv = -4.0 * phys::pi * phys::rho_w / (3.0 * g.dV * rd) * sum;
         rvc = t.rv + drv;
         thc = t.th + drv * t.dth_drv;
     }
-    bad |= !isfinite(rvc) || !isfinite(thc);
+    bad |= live && (!isfinite(rvc) || !isfinite(thc));
     const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
     const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
     const unsigned anybad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
+    if (live && sl == 0) {
         th[c] = thc;
         rv[c] = rvc;
+    }
+    if (lane == 0) {
         if (ne) atomicAdd(&st->n_euler, (unsigned long long)ne);
         if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
         if (anybad) atomicOr(&st->flags, kFlagNumeric);
@@ -443,13 +521,32 @@ cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t
     return cudaGetLastError();
 }
 
+template <int LPC>
+static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
+    const int64_t threads = ((int64_t)c->grid.n_cells * LPC + 31) / 32 * 32;
+    k_condense<LPC><<<grid_for(threads, B), B, 0, c->stream>>>(
+        c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
+        c->oi.cond_solver, c->oi.precision == SDM_PRECISION_MIXED, c->dstats);
+}
+
+// Lanes per cell: about eight super-droplets per lane, doubled while the
+// launch has fewer than ~54 warps per SM (152 SMs), since one lane's solves
+// run in sequence and the FP64 pipe needs several warps per scheduler.
+// One-warp blocks when cells are few, so that the last wave is fine-grained.
 cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
-    const int B = 128;
-    const int64_t threads = (int64_t)c->grid.n_cells * 32;
-    k_condense<<<grid_for(threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, c->th, c->rv,
-                                                          c->rhod, c->grid, o.sstp_cond, o.RH_max,
-                                                          c->oi.physics, c->oi.cond_solver,
-                                                          c->oi.precision == SDM_PRECISION_MIXED, c->dstats);
+    const int64_t per_cell = (int64_t)c->G * c->oi.sd_conc, n_cells = c->grid.n_cells;
+    int lpc = 1;
+    while (lpc < 32 && lpc * 8 < per_cell) lpc *= 2;
+    while (lpc < 32 && n_cells * lpc < (int64_t)32 * 8192) lpc *= 2;
+    const int B = n_cells * lpc < (int64_t)32 * 32768 ? 32 : 128;
+    switch (lpc) {
+        case 1: launch_condense_lpc<1>(c, o, B); break;
+        case 2: launch_condense_lpc<2>(c, o, B); break;
+        case 4: launch_condense_lpc<4>(c, o, B); break;
+        case 8: launch_condense_lpc<8>(c, o, B); break;
+        case 16: launch_condense_lpc<16>(c, o, B); break;
+        default: launch_condense_lpc<32>(c, o, B); break;
+    }
     return cudaGetLastError();
 }
 

@@ -130,4 +130,7 @@ template cudaError_t radix_sort_pairs<unsigned long long>(unsigned long long *, 
                                                           unsigned long long *, uint32_t *, uint32_t *,
                                                           int64_t, int, int, uint32_t *, uint32_t *,
                                                           cudaStream_t);
+template cudaError_t radix_sort_pairs<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, uint32_t *,
+                                                uint32_t *, int64_t, int, int, uint32_t *, uint32_t *,
+                                                cudaStream_t);
 }  // namespace sdm

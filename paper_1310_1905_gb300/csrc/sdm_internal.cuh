@@ -276,8 +276,7 @@ cudaError_t scan_counts(const uint32_t *count, uint32_t *offset, uint32_t *tmp, 
 struct MemberDev {
     uint32_t off, n;         // super-droplet range
     uint32_t tile0, ntiles;  // condensation tiles
-    uint32_t active;         // super-droplets with N > 0 (per substep)
-    uint32_t zeros;
+    uint32_t zeros;          // multiplicities that reached zero, not yet recycled
     double dV, md;           // volume [m^3], dry-air mass [kg]
     double th, rv, rhod;
     double nu, cX;           // air viscosity and Best-number factor for v_t

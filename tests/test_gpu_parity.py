@@ -61,6 +61,38 @@ def test_condensation_matches_oracle(solver):
     assert np.abs(o.rv - w.rv.ravel()).max() > 1e-6  # something condensed
 
 
+def test_condensation_several_roots():
+    """A 25 nm haze droplet (r_d = 13 nm, kappa 0.61) at S = 1.0088, just
+    below its critical supersaturation, with dt' = 0.1 s: over the bracket of
+    eq. rw2_implicit the residual changes sign three times (near 2.0e-15,
+    2.7e-14 and 5.0e-14 m^2).  The bisection ends at the first; a solver
+    that polishes from wherever FP32 stops deciding ends at the third.  The
+    droplet and the ambient state are one the 2D case reaches in its first
+    substep (level z = 810 m)."""
+    w = workloads.icmw_2d(nx=2, nz=2, sd_conc=3, seed=1, dt=0.1)
+    w.th[...] = 289.0
+    w.rv[...] = 7.5e-3
+    w.rhod[...] = 1.1275719998589389
+    for solver in ("fast", "bisect"):
+        w.cfg["cond_solver"] = solver
+        p, o = pair(w)
+        n = len(o.state.N)
+        vals = dict(rw2=6.5206016327642645e-16, rd3=2.3321073379471742e-24, kappa=0.61)
+        for k, v in vals.items():
+            sdm.sdm_set_attr(p.ctx, k, np.full(n, v))
+            getattr(o.state, k)[:] = v
+        sdm.sdm_set_attr(p.ctx, "N", np.full(n, 12609913, np.uint64))
+        o.state.N[:] = 12609913
+        th, rv = w.th.copy(), w.rv.copy()
+        one = dict(COND_ONLY, sstp_cond=1, sstp_coal=1)
+        p.step_sync(one, th, rv)
+        o.step_sync(one)
+        r = oracle_state(o, present_dims(w.cfg))
+        assert 1.9e-15 < r["rw2"][0] < 2.1e-15, r["rw2"][0]  # the first root
+        compare_states(p.state(), r)
+        assert_close("r_v", rv.ravel(), o.rv)
+
+
 def test_condensation_bare_maxwell_mason():
     w = workloads.icmw_2d(nx=5, nz=11, sd_conc=12, seed=4, dz=130.0, physics=0)
     p, o = pair(w)
