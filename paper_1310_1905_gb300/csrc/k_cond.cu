@@ -121,14 +121,15 @@ struct SolveCounters {
 //   a_w = num / den,
 // so that g = 2 a b (rho_v den - rho_vs num e^(A/r)) / (rho_w (b D_M + Dterm a D_T) den)
 // takes one division where the term-by-term form takes about ten.  It equals
-// growth() up to rounding.
-SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, int physics) {
+// growth() up to rounding.  Coef holds the factor 2 D_eff / rho_w as the
+// fraction (2 a b) / (rho_w (b D_M + Dterm a D_T)), numerator and denominator
+// apart.
+struct Coef {
+    double n, d;
+};
+
+SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
     using namespace phys;
-    const double r = sqrt(x);
-    const double rinv = 1.0 / r;
-    const double r3 = x * r;
-    const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
-    const double kel = exp(t.A * rinv);
     double a = D0, b = K0, DM = 1.0, DT = 1.0;
     if (physics) {
         const double c1 = 4.0 / 3.0 + 0.377, c2 = 4.0 / 3.0;
@@ -145,8 +146,56 @@ SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, i
         a = D0 * (1.0 + KnM) * Sh * 0.5;
         b = K0 * (1.0 + KnT) * Nu * 0.5;
     }
-    return 2.0 * a * b * (t.rho_v_eff * den - t.rho_vs * num * kel) /
-           (rho_w * (b * DM + t.Dterm * a * DT) * den);
+    return Coef{2.0 * a * b, rho_w * (b * DM + t.Dterm * a * DT)};
+}
+
+SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, int physics) {
+    const double r = sqrt(x);
+    const double rinv = 1.0 / r;
+    const double r3 = x * r;
+    const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
+    const double kel = exp(t.A * rinv);
+    const Coef c = growth_coef(rinv, r3, t, physics);
+    return c.n * (t.rho_v_eff * den - t.rho_vs * num * kel) / (c.d * den);
+}
+
+// g(x0) for the bracket and the Euler step: the difference rho_v - rho_o,
+// where all the cancellation is, takes the operations of growth() one by
+// one; the factor 2 D_eff / rho_w, which only scales it, comes from
+// growth_coef (it differs from growth()'s by rounding, a relative 1e-16 of
+// g, which moves the Euler step by a relative 1e-16 of its increment)
+SDM_HD double growth_g0(double x, double rd3, double kappa, const Thermo &t, int physics) {
+    const double r = sqrt(x);
+    const double r3 = x * r;
+    const double aw = (r3 - rd3) / (r3 - rd3 * (1.0 - kappa));
+    const double rho_o = t.rho_vs * aw * exp(t.A / r);
+    const Coef c = growth_coef(1.0 / r, r3, t, physics);
+    return c.n / c.d * (t.rho_v_eff - rho_o);
+}
+
+// The FP32 growth rate with its error bound and dg/dx.
+struct GF {
+    float g, err, dg;
+};
+
+SDM_HD GF growth_f3(float x, float rd3, float kappa, const ThermoF &t, int physics) {
+    GF r;
+    r.g = growth_f(x, rd3, kappa, t, physics, &r.err, &r.dg);
+    return r;
+}
+
+// Out-of-line copies for the less frequent call sites keep the kernels'
+// hot code small (their main stall is instruction fetch); the ambient
+// state is passed by address (it lives in shared memory in the kernels).
+SDM_HD __noinline__ GF growth_f3_call(float x, float rd3, float kappa, const ThermoF *t, int physics) {
+    return growth_f3(x, rd3, kappa, *t, physics);
+}
+
+// the FP64 residual with the term-by-term growth rate, on the rare paths
+// (undecided bracket ends, replay decisions, the bisection fallback)
+SDM_HD __noinline__ double fres_rare(double x, double x0, double rd3, double kappa, const Thermo *t,
+                                     double dtp, int physics) {
+    return fres(x, x0, rd3, kappa, *t, dtp, physics);
 }
 
 SDM_HD double fres_fast(double x, double x0, double rd3, double kappa, const Thermo &t, double dtp,
@@ -156,55 +205,62 @@ SDM_HD double fres_fast(double x, double x0, double rd3, double kappa, const The
 
 __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
                                           const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
-    // g(x0) with the term-by-term formula: it sets the bracket and, when the
-    // bracket is ill-posed, the result itself, where its rounding is not
-    // damped by the stiffness of the implicit equation
-    const double g0 = growth(x0, rd3, kappa, t, physics);
+    // g(x0) sets the bracket and, when the bracket is ill-posed, the result
+    // itself, where its rounding is not damped by the stiffness of the
+    // implicit equation: its rho_v - rho_o is formed as growth() forms it
+    const double g0 = growth_g0(x0, rd3, kappa, t, physics);
     const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
     const float rd3f = (float)rd3, kf = (float)kappa, dtpf = (float)dtp, x0f = (float)x0;
-    // sign of f at the point x0 + d (d an FP32 increment) computed in FP32
-    // and trusted where |f| exceeds its error bound: it is then the sign an
-    // FP64 evaluation gives; *noise is that bound
-    auto positive = [&](float d, bool *decided, float *noise) -> bool {
-        float eg;
-        const float g = growth_f(x0f + d, rd3f, kf, tf, physics, &eg, nullptr);
-        const float f = d - dtpf * g;
-        *noise = 2.4e-7f * fabsf(d) + 4.0f * dtpf * eg;
-        *decided = fabsf(f) > *noise;
-        return f > 0.0f;
-    };
-    bool ok;
-    float nz;
-    // at x0 itself f = -dtp g0 exactly
-    auto end_sign = [&](double x) -> bool {
-        if (x == x0) return -dtp * g0 > 0.0;
-        const bool p = positive((float)(x - x0), &ok, &nz);
-        return ok ? p : fres(x, x0, rd3, kappa, t, dtp, physics) > 0.0;
-    };
-    const bool pa = end_sign(a), pb = end_sign(b);
-    if (pa == pb) {
-        cnt.euler++;
-        return 0.5 * (a + b);
-    }
-    const bool plo = pa;
-    if (b - a <= 0x1p-52 * b) return 0.5 * (a + b);  // the bisection's own first exit
-    // 1. locate: halve the increment's bracket in FP32 while the signs are
-    //    decided (the same halves the FP64 bisection takes, up to FP32
-    //    rounding of the midpoints)
-    float L = (float)(a - x0), H = (float)(b - x0), mu = 0.0f;
-    bool undecided = false;
-    for (int it = 0; it < 64; ++it) {
-        const float m = 0.5f * (L + H);
-        if (!(m > L && m < H)) break;
-        const bool pm = positive(m, &ok, &nz);
-        if (!ok) {
-            mu = m;
-            undecided = true;
-            break;
+    // 1. ends and locate.  The sign of f at x0 + d (d an FP32 increment) is
+    //    computed in FP32 and trusted where |f| exceeds its error bound (it
+    //    is then the sign an FP64 evaluation gives).  Points k = 0, 1 are the
+    //    bracket's ends (at x0 itself f = -dtp g0 exactly); from k = 2 the
+    //    increment's bracket is halved while FP32 decides - the halves the
+    //    FP64 bisection takes, up to FP32 rounding of the midpoints.
+    float L = (float)(a - x0), H = (float)(b - x0), mu = 0.0f, dg_last = 0.0f;
+    bool pa = false, plo = false, undecided = false;
+    for (int k = 0; k < 66; ++k) {
+        float d;
+        if (k < 2) {
+            d = k ? H : L;
+        } else {
+            d = 0.5f * (L + H);
+            if (!(d > L && d < H)) break;
         }
-        if (pm == plo) L = m;
-        else H = m;
+        bool p;
+        const double xe = k ? b : a;
+        if (k < 2 && xe == x0) {
+            p = -dtp * g0 > 0.0;
+        } else {
+            const GF q = growth_f3(x0f + d, rd3f, kf, tf, physics);
+            const float f = d - dtpf * q.g;
+            dg_last = q.dg;
+            p = f > 0.0f;
+            if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
+                if (k < 2) {
+                    p = fres_rare(xe, x0, rd3, kappa, &t, dtp, physics) > 0.0;
+                } else {
+                    mu = d;
+                    undecided = true;
+                    break;
+                }
+            }
+        }
+        if (k == 0) {
+            pa = p;
+        } else if (k == 1) {
+            if (pa == p) {  // f keeps its strict sign: the Euler step
+                cnt.euler++;
+                return 0.5 * (a + b);
+            }
+            plo = pa;
+            if (b - a <= 0x1p-52 * b) return 0.5 * (a + b);  // the bisection's own first exit
+        } else if (p == plo) {
+            L = d;
+        } else {
+            H = d;
+        }
     }
     const float Lu = L, Hu = H;
     if (!undecided) mu = 0.5f * (L + H);
@@ -215,11 +271,13 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     double xk = x0 + (double)mu;
     const bool mu_inside = xk > lo && xk < hi;
     if (!mu_inside) xk = 0.5 * (lo + hi);
-    double fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
-    const bool pmu = fk > 0.0;  // the FP64 sign at mu, needed by the replay
-    double xp = 0.0, fp = 0.0, slope = 1.0, r = 0.0;
-    bool have_prev = false, settled = false;
-    for (int k = 0; k < 12 && !settled; ++k) {
+    bool pmu = false;  // the FP64 sign at mu, needed by the replay
+    double xp = 0.0, fp = 0.0, slope = 1.0 - dtp * (double)dg_last, r = 0.0;
+    double sdx = 1.0, sdf = 1.0;  // the last secant's steps
+    bool settled = false, have_slope = true;  // else the slope is sdf / sdx
+    for (int k = 0; k < 13; ++k) {
+        const double fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
+        if (k == 0) pmu = fk > 0.0;
         if (fk == 0.0) {
             r = xk;
             settled = true;
@@ -232,16 +290,17 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
             settled = true;
             break;
         }
+        if (k == 12) break;
+        // Newton with the FP32 derivative of the last FP32 evaluation first,
+        // then secant steps
+        const bool secant = k > 0 && fk != fp;
         double xn;
-        bool secant = false;
-        if (have_prev && fk != fp) {
-            slope = (fk - fp) / (xk - xp);
-            xn = xk - fk / slope;
-            secant = true;
+        if (secant) {
+            sdx = xk - xp;
+            sdf = fk - fp;
+            xn = xk - fk * (sdx / sdf);
+            have_slope = false;
         } else {
-            float eg, dg;
-            growth_f((float)xk, rd3f, kf, tf, physics, &eg, &dg);
-            slope = 1.0 - dtp * (double)dg;  // approximate f'
             xn = slope != 0.0 ? xk - fk / slope : 0.5 * (lo + hi);
         }
         // a step past an end of the bracket says the root hugs that end
@@ -265,9 +324,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         }
         xp = xk;
         fp = fk;
-        have_prev = true;
         xk = xn;
-        fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
     }
     // 3. replay: near activation f need not be monotonic, and a bracket can
     //    hold several roots.  The polish found the one nearest mu; the
@@ -287,15 +344,17 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
             if (pmu == plo) RL = mu;
             else RH = mu;
         }
-        const double sl = fabs(slope);
         for (int it = 0; it < 64 && consistent; ++it) {
             const float m = 0.5f * (RL + RH);
             if (!(m > RL && m < RH) || fabsf(m - dr) <= dtol) break;
-            bool pm = positive(m, &ok, &nz);
-            if (!ok) {
+            const GF q = growth_f3_call(x0f + m, rd3f, kf, &tf, physics);
+            const float f = m - dtpf * q.g, nz = 2.4e-7f * fabsf(m) + 4.0f * dtpf * q.err;
+            bool pm = f > 0.0f;
+            if (!(fabsf(f) > nz)) {
                 // within a few noise widths of r: the halvings close in on r
+                const double sl = fabs(have_slope ? slope : sdf / sdx);
                 if ((double)fabsf(m - dr) * sl <= 8.0 * (double)nz) break;
-                pm = fres(x0 + (double)m, x0, rd3, kappa, t, dtp, physics) > 0.0;
+                pm = fres_rare(x0 + (double)m, x0, rd3, kappa, &t, dtp, physics) > 0.0;
             }
             if (pm != (plo == (m < dr))) {
                 consistent = false;
@@ -320,7 +379,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         if (hi - lo <= 0x1p-52 * hi) break;
         const double m = 0.5 * (lo + hi);
         if (!(m > lo && m < hi)) break;
-        if ((fres(m, x0, rd3, kappa, t, dtp, physics) > 0.0) == plo) lo = m;
+        if ((fres_rare(m, x0, rd3, kappa, &t, dtp, physics) > 0.0) == plo) lo = m;
         else hi = m;
     }
     return 0.5 * (lo + hi);
@@ -335,15 +394,14 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
 __host__ __device__ bool solve_rw2_f32(double x0, double rd3, double kappa, const ThermoF &tf,
                                        float dtp, int physics, double *x1, SolveCounters &cnt) {
     const float rd3f = (float)rd3, kf = (float)kappa;
-    float eg, dg;
-    const float g0 = growth_f((float)x0, rd3f, kf, tf, physics, &eg, nullptr);
+    const float g0 = growth_f3_call((float)x0, rd3f, kf, &tf, physics).g;
     const float rdf = cbrtf(rd3f);
     const float lo_d = fmaxf((float)((double)(rdf * rdf) - x0), fminf(2.0f * dtp * g0, 0.0f));
     const float hi_d = fmaxf(2.0f * dtp * g0, 0.0f);
     auto f = [&](float d, float *der) -> float {
-        const float g = growth_f((float)(x0 + (double)d), rd3f, kf, tf, physics, &eg, der ? &dg : nullptr);
-        if (der) *der = 1.0f - dtp * dg;
-        return d - dtp * g;
+        const GF q = growth_f3((float)(x0 + (double)d), rd3f, kf, tf, physics);
+        if (der) *der = 1.0f - dtp * q.dg;
+        return d - dtp * q.g;
     };
     const float fa = f(lo_d, nullptr), fb = f(hi_d, nullptr);
     if ((fa > 0.0f) == (fb > 0.0f)) {
@@ -397,10 +455,31 @@ __device__ __forceinline__ double warp_sum(double v) {
 // thermodynamics and sum through shuffles inside the group.  Fewer lanes per
 // cell give each lane more super-droplets, which evens out the solve's
 // data-dependent cost across the warp.
-template <int LPC>
-__global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
-                           const double *rhod, Grid g, int sstp, double RH_max, int physics,
-                           int solver, int mixed, DevStats *st) {
+// MODE: the solver, fixed at compile time so that each kernel carries only
+// its own code.
+enum { kModeBisect = 0, kModeFast = 1, kModeMixed = 2 };
+
+template <int MODE>
+__device__ __forceinline__ double solve_mode(double x0, double rd3, double kappa, const Thermo &t,
+                                             const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
+    double x1;
+    if (MODE == kModeMixed && !near_activation(x0, rd3, kappa, t)) {
+        solve_rw2_f32(x0, rd3, kappa, tf, (float)dtp, physics, &x1, cnt);
+    } else if (MODE == kModeBisect) {
+        int eu = 0;
+        x1 = solve_rw2_bisect(x0, rd3, kappa, t, dtp, physics, &eu);
+        cnt.euler += eu;
+    } else {
+        x1 = solve_rw2_fast(x0, rd3, kappa, t, tf, dtp, physics, cnt);
+    }
+    return x1;
+}
+
+constexpr int kMaxBlock = 128;
+
+template <int LPC, int MODE>
+__global__ void __launch_bounds__(kMaxBlock, 5) k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
+                           const double *rhod, Grid g, int sstp, double RH_max, int physics, DevStats *st) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int sl = lane % LPC;
@@ -413,24 +492,29 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
     const double dtp = g.dt / sstp;
     SolveCounters cnt{0, 0};
     bool bad = false;
+    // the cell's ambient state for the solves sits in shared memory: read
+    // there by reference it takes no registers across the solve
+    __shared__ Thermo s_t[kMaxBlock / LPC];
+    __shared__ ThermoF s_tf[kMaxBlock / LPC];
+    const int gi = threadIdx.x / LPC;
+    const Thermo &t = s_t[gi];
+    const ThermoF &tf = s_tf[gi];
+    const double rdf = rhod_factor(rd);
     for (int sub = 0; sub < sstp; ++sub) {
-        const Thermo t = thermo_eval(thc, rvc, rd, RH_max);
-        const ThermoF tf = to_float(t);
+        {
+            const Thermo tt = thermo_eval_f<true>(thc, rvc, rd, RH_max, rdf);
+            if (sl == 0) {
+                s_t[gi] = tt;
+                s_tf[gi] = to_float(tt);
+            }
+        }
+        __syncwarp();
         double sum = 0.0;
         for (uint32_t i = beg + sl; i < end; i += LPC) {
             const unsigned long long N = s.N[i];
             if (N == 0) continue;
             const double x0 = s.rw2[i];
-            double x1;
-            if (mixed && !near_activation(x0, s.rd3[i], s.kappa[i], t)) {
-                solve_rw2_f32(x0, s.rd3[i], s.kappa[i], tf, (float)dtp, physics, &x1, cnt);
-            } else if (solver == 0) {
-                int eu = 0;
-                x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, physics, &eu);
-                cnt.euler += eu;
-            } else {
-                x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
-            }
+            const double x1 = solve_mode<MODE>(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
             bad |= !isfinite(x1);
             s.rw2[i] = x1;
             sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
@@ -440,6 +524,7 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
         const double drv = -4.0 * phys::pi * phys::rho_w / (3.0 * g.dV * rd) * sum;
         rvc = t.rv + drv;
         thc = t.th + drv * t.dth_drv;
+        __syncwarp();  // every lane has read s_t before the next substep writes it
     }
     bad |= live && (!isfinite(rvc) || !isfinite(thc));
     const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
@@ -459,6 +544,7 @@ __global__ void k_condense(SdArrays s, const uint32_t *offset, double *th, doubl
 // Ensemble condensation, one substep: a block per tile (tiles never straddle
 // two members), the member's thermodynamics computed once per block, a
 // deterministic block sum of N (r_w^3[new] - r_w^3[old]) into tile_sum.
+template <int MODE>
 __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,
                                  const uint32_t *tile_beg, const uint32_t *tile_end, double *tile_sum,
                                  EnsCondParams p, DevStats *st) {
@@ -466,10 +552,14 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
     __shared__ double s_part[32];
     const int tile = blockIdx.x;
     const MemberDev &md = M[tile_member[tile]];
-    if (threadIdx.x == 0) s_t = thermo_eval(md.th, md.rv, md.rhod, p.RH_max);
+    __shared__ ThermoF s_tf;
+    if (threadIdx.x == 0) {
+        s_t = thermo_eval_f<true>(md.th, md.rv, md.rhod, p.RH_max, rhod_factor(md.rhod));
+        s_tf = to_float(s_t);
+    }
     __syncthreads();
-    const Thermo t = s_t;
-    const ThermoF tf = to_float(t);
+    const Thermo &t = s_t;
+    const ThermoF &tf = s_tf;
     const double dtp = p.dt / p.sstp;
     SolveCounters cnt{0, 0};
     double sum = 0.0;
@@ -478,16 +568,7 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
         const unsigned long long N = s.N[i];
         if (N == 0) continue;
         const double x0 = s.rw2[i];
-        double x1;
-        if (p.mixed && !near_activation(x0, s.rd3[i], s.kappa[i], t)) {
-            solve_rw2_f32(x0, s.rd3[i], s.kappa[i], tf, (float)dtp, p.physics, &x1, cnt);
-        } else if (p.solver == 0) {
-            int eu = 0;
-            x1 = solve_rw2_bisect(x0, s.rd3[i], s.kappa[i], t, dtp, p.physics, &eu);
-            cnt.euler += eu;
-        } else {
-            x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, p.physics, cnt);
-        }
+        const double x1 = solve_mode<MODE>(x0, s.rd3[i], s.kappa[i], t, tf, dtp, p.physics, cnt);
         bad |= !isfinite(x1);
         s.rw2[i] = x1;
         sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
@@ -516,37 +597,46 @@ cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t
                                   int n_tiles, int threads, EnsCondParams p, DevStats *st,
                                   cudaStream_t stream) {
     if (n_tiles == 0) return cudaSuccess;
-    k_ens_cond_tiles<<<n_tiles, threads, 0, stream>>>(s, M, tile_member, tile_beg, tile_end, tile_sum, p,
-                                                       st);
+    if (p.mixed)
+        k_ens_cond_tiles<kModeMixed><<<n_tiles, threads, 0, stream>>>(s, M, tile_member, tile_beg, tile_end,
+                                                                      tile_sum, p, st);
+    else if (p.solver == 0)
+        k_ens_cond_tiles<kModeBisect><<<n_tiles, threads, 0, stream>>>(s, M, tile_member, tile_beg, tile_end,
+                                                                       tile_sum, p, st);
+    else
+        k_ens_cond_tiles<kModeFast><<<n_tiles, threads, 0, stream>>>(s, M, tile_member, tile_beg, tile_end,
+                                                                     tile_sum, p, st);
     return cudaGetLastError();
 }
 
-template <int LPC>
+template <int LPC, int MODE>
 static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
     const int64_t threads = ((int64_t)c->grid.n_cells * LPC + 31) / 32 * 32;
-    k_condense<LPC><<<grid_for(threads, B), B, 0, c->stream>>>(
+    k_condense<LPC, MODE><<<grid_for(threads, B), B, 0, c->stream>>>(
         c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
-        c->oi.cond_solver, c->oi.precision == SDM_PRECISION_MIXED, c->dstats);
+        c->dstats);
 }
 
-// Lanes per cell: about eight super-droplets per lane, doubled while the
-// launch has fewer than ~54 warps per SM (152 SMs), since one lane's solves
-// run in sequence and the FP64 pipe needs several warps per scheduler.
-// One-warp blocks when cells are few, so that the last wave is fine-grained.
+template <int MODE>
+static void launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) {
+    if (lpc == 4) launch_condense_lpc<4, MODE>(c, o, B);
+    else if (lpc == 8) launch_condense_lpc<8, MODE>(c, o, B);
+    else launch_condense_lpc<32, MODE>(c, o, B);
+}
+
+// Lanes per cell: 4, 8 or 32 (about eight super-droplets per lane), raised
+// while the launch has fewer than ~54 warps per SM (152 SMs), since one
+// lane's solves run in sequence and the FP64 pipe needs several warps per
+// scheduler.  One-warp blocks when cells are few, so that the last wave is
+// fine-grained.
 cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
     const int64_t per_cell = (int64_t)c->G * c->oi.sd_conc, n_cells = c->grid.n_cells;
-    int lpc = 1;
-    while (lpc < 32 && lpc * 8 < per_cell) lpc *= 2;
-    while (lpc < 32 && n_cells * lpc < (int64_t)32 * 8192) lpc *= 2;
+    int lpc = per_cell <= 32 ? 4 : (per_cell <= 64 ? 8 : 32);
+    while (lpc < 32 && n_cells * lpc < (int64_t)32 * 8192) lpc = lpc == 4 ? 8 : 32;
     const int B = n_cells * lpc < (int64_t)32 * 32768 ? 32 : 128;
-    switch (lpc) {
-        case 1: launch_condense_lpc<1>(c, o, B); break;
-        case 2: launch_condense_lpc<2>(c, o, B); break;
-        case 4: launch_condense_lpc<4>(c, o, B); break;
-        case 8: launch_condense_lpc<8>(c, o, B); break;
-        case 16: launch_condense_lpc<16>(c, o, B); break;
-        default: launch_condense_lpc<32>(c, o, B); break;
-    }
+    if (c->oi.precision == SDM_PRECISION_MIXED) launch_condense_mode<kModeMixed>(c, o, lpc, B);
+    else if (c->oi.cond_solver == SDM_SOLVER_BISECT) launch_condense_mode<kModeBisect>(c, o, lpc, B);
+    else launch_condense_mode<kModeFast>(c, o, lpc, B);
     return cudaGetLastError();
 }
 

@@ -83,14 +83,25 @@ struct Thermo {
     double rho_a, nu, lambda_D, lambda_K, Sc, Pr, cX;
 };
 
+// (rho_d R_d / p1000)^(R_d / c_pd): the rho_d factor of T in Appendix A,
+// constant over a step (rho_d changes only between steps)
+SDM_HD double rhod_factor(double rhod) {
+    using namespace phys;
+    return pow(rhod * R_d / p1000, R_d / c_pd);
+}
+
 // Appendix A: T and p from theta, r_v, rho_d; Sec. 5.1.3 quantities.
-SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
+// fast_mu: the viscosity's (T/273)^1.5 as x sqrt(x) rather than pow; mu
+// only scales D_eff's ventilation terms, so the condensation kernels take
+// it (the coalescence ambient keeps pow).
+template <bool fast_mu = false>
+SDM_HD Thermo thermo_eval_f(double th, double rv, double rhod, double RH_max, double rhod_f) {
     using namespace phys;
     Thermo t;
     t.th = th;
     t.rv = rv;
     t.rhod = rhod;
-    t.T = pow(th * pow(rhod * R_d / p1000, R_d / c_pd), c_pd / (c_pd - R_d));
+    t.T = pow(th * rhod_f, c_pd / (c_pd - R_d));
     t.lv = l_v0 + (c_pv - c_l) * (t.T - T0);
     // Clausius-Clapeyron integrated with the linear l_v(T)
     const double lnp = (l_v0 + (c_l - c_pv) * T0) / R_v * (1.0 / T0 - 1.0 / t.T) -
@@ -102,7 +113,8 @@ SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
     t.A = 2.0 * sigma_w / (R_v * t.T * rho_w);
     t.Dterm = t.rho_vs * t.lv / t.T * (t.lv / (R_v * t.T) - 1.0);
     t.rho_a = rhod * (1.0 + rv);
-    const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * pow(t.T / 273.0, 1.5);
+    const double Tr = t.T / 273.0;
+    const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * (fast_mu ? Tr * sqrt(Tr) : pow(Tr, 1.5));
     t.nu = mu / t.rho_a;
     t.lambda_D = 2.0 * D0 / sqrt(8.0 * R_v * t.T / pi);
     t.lambda_K = 2.0 * K0 / (t.rho_a * c_pd * sqrt(8.0 * R_d * t.T / pi));
@@ -110,6 +122,10 @@ SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
     t.Pr = t.nu * t.rho_a * c_pd / K0;
     t.cX = 32.0 / 3.0 * (rho_w - t.rho_a) / t.rho_a * grav / (t.nu * t.nu);
     return t;
+}
+
+SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
+    return thermo_eval_f<false>(th, rv, rhod, RH_max, rhod_factor(rhod));
 }
 
 // Khvorostyanov & Curry (2002) sphere: Re(X), X = cX r^3 (Best number)

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads
-from gpu_helpers import assert_close, gpu_particles, rounding_ambiguous
+from gpu_helpers import RTOL, assert_close, gpu_particles, rounding_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +32,27 @@ def oracle_cells(w, cells):
     st, nreal = o.init_cells(o.th, o.rv, o.rhod, cells, with_nreal=True)
     o.state = st
     return o, nreal
+
+
+def ulp_spread(w, cells, opts, name="rw2", ulps=4):
+    """How far the oracle's own result moves when theta changes by a few
+    ulps in the sampled cells (after initialisation, before the step): the
+    part of the FP64 answer that its inputs' last bits decide.  The two
+    sides' temperatures and saturation densities differ by about that much
+    (exp and pow round differently in the two math libraries).  Near
+    activation the growth rate is a small difference of nearly equal vapour
+    densities and this spread exceeds 1e-12 for a few droplets."""
+    base, _ = oracle_cells(w, cells)
+    base.step_sync(opts)
+    ref = getattr(base.state.sorted_by_uid(), name)
+    spread = np.zeros_like(ref)
+    for direction in (np.inf, -np.inf):
+        o, _ = oracle_cells(w, cells)
+        for _ in range(ulps):
+            o.th[cells] = np.nextafter(o.th[cells], direction)
+        o.step_sync(opts)
+        spread = np.maximum(spread, np.abs(getattr(o.state.sorted_by_uid(), name) - ref))
+    return ref, spread
 
 
 def workload(name):
@@ -69,7 +90,19 @@ def test_full_size_sampled_cells(name):
     _, g = by_uid(p, ["rw2"])
     s = o.state.sorted_by_uid()
     m = np.isin(s.uid.astype(np.int64), ksel)
-    assert_close("rw2 after condensation", g["rw2"][s.uid[m].astype(np.int64)], s.rw2[m])
+    # 1e-12 relative, or the oracle's own spread under a few ulps of theta
+    # where that is wider
+    ref, spread = ulp_spread(w, keep, COND)
+    assert np.array_equal(ref, s.rw2[m])
+    wide = spread > RTOL * ref
+    assert wide.mean() < 0.05, f"{wide.sum()} of {wide.size} droplets are ill-conditioned"
+    got = g["rw2"][s.uid[m].astype(np.int64)]
+    err = np.abs(got - ref)
+    tol = np.maximum(RTOL * ref, spread)
+    assert (err <= tol).all(), f"rw2 after condensation: {(err > tol).sum()} of {err.size} outside " \
+                               f"max(1e-12, spread); worst rel {np.max(err / ref):.3e}"
+    print(f"{name}: {wide.sum()} of {wide.size} droplets wider than 1e-12 under a 4-ulp change of theta; "
+          f"GPU-oracle worst rel {np.max(err / ref):.3e}, worst outside 1e-12 {np.max((err / ref)[~wide]):.3e}")
     # coalescence (all substeps) from the initial state on both
     p2 = gpu_particles(w)
     p2.step_async(COAL)
