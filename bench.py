@@ -40,9 +40,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (4 FP64 flops) per SM per clock
 FP64_FLOPS_PER_SM_CLK = 4.0
 N_SM = 152
-# ncu, k_condense on the 2D case (profiles/k_condense_icmw_2d_fp64.md)
-COND_FP64_FLOPS_PER_SD_SUBSTEP = 1381.0
-COND_DRAM_BYTES_PER_LAUNCH = 11.87e6
+# ncu, k_condense on the 2D case (profiles/k_condense_icmw_2d_fp64.md):
+# FP64 flops the kernel executes (2 DFMA + DADD + DMUL) per SD-substep, and
+# DRAM bytes read + written per launch
+COND_FP64_FLOPS_PER_SD_SUBSTEP = 1005.3
+COND_DRAM_BYTES_PER_LAUNCH = 11.81e6
 
 
 def parse():

@@ -1008,7 +1008,9 @@ sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *o, int *tile_out, int *t
     cudaEventCreate(&b);
     float best = 1e30f;
     int bt = e->tile, bth = e->cond_threads;
+    const int max_threads = ens_cond_max_threads(p);
     for (auto &c : cand) {
+        if (c[1] > max_threads) continue;
         e->tile = c[0];
         e->cond_threads = c[1];
         if (sdm_status s = push_tables(e)) return s;

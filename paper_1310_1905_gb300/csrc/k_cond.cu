@@ -1,7 +1,7 @@
-// Condensation / evaporation (paper Sec. 5.1.3): one warp per grid cell,
-// all sstp_cond substeps in one launch.  In each substep every lane advances
-// its super-droplets' r_w^2 with the implicit growth equation (eq.
-// rw2_implicit), the warp sums N (r_w^3[new] - r_w^3[old]) and every lane
+// Condensation / evaporation (paper Sec. 5.1.3): a group of lanes per grid
+// cell, all sstp_cond substeps in one launch.  In each substep every lane
+// advances its super-droplets' r_w^2 with the implicit growth equation (eq.
+// rw2_implicit), the group sums N (r_w^3[new] - r_w^3[old]) and every lane
 // applies eq. (rhov_update) to its register copy of the cell's r_v, theta.
 #include "sdm_internal.cuh"
 
@@ -128,6 +128,22 @@ struct Coef {
     double n, d;
 };
 
+// (1 + y)^(1/3) - 1 for 0 <= y <= 1/64 by its binomial series to y^8
+// (remainder below 5e-17 y, i.e. 2e-19 of Sh): the growth rate's ventilation
+// factors take it for small droplets, where cbrt(1 + y) would spend an FP64
+// cube root on a number within 2% of one
+SDM_HD double cbrt1p_small(double y) {
+    return y * (1.0 / 3 + y * (-1.0 / 9 + y * (5.0 / 81 + y * (-10.0 / 243 + y * (22.0 / 729 +
+           y * (-154.0 / 6561 + y * (374.0 / 19683 + y * (-935.0 / 59049))))))));
+}
+
+// sqrt(1 + e) - 1 for 0 <= e <= 1/64 by its binomial series to e^9
+// (remainder below 6e-19 e)
+SDM_HD double sqrt1pm1_small(double e) {
+    return e * (0.5 + e * (-1.0 / 8 + e * (1.0 / 16 + e * (-5.0 / 128 + e * (7.0 / 256 + e * (-21.0 / 1024 +
+           e * (33.0 / 2048 + e * (-429.0 / 32768 + e * (715.0 / 65536)))))))));
+}
+
 SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
     using namespace phys;
     double a = D0, b = K0, DM = 1.0, DT = 1.0;
@@ -138,11 +154,18 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
         DT = 1.0 + c1 * KnT + c2 * KnT * KnT;
         const double X = t.cX * r3;
         const double e = 4.0 / (delta0 * delta0 * sqrt(C0)) * sqrt(X);
-        const double s = e / (sqrt(1.0 + e) + 1.0);
+        // Re = delta0^2/4 (sqrt(1 + e) - 1)^2 (KC2002)
+        const double s = e <= 0.015625 ? sqrt1pm1_small(e) : e / (sqrt(1.0 + e) + 1.0);
         const double Re = delta0 * delta0 / 4.0 * s * s;
-        const double fRe = Re > 1.0 ? pow(Re, 0.077) : 1.0;
-        const double Sh = 1.0 + cbrt(1.0 + Re * t.Sc) * fRe;
-        const double Nu = 1.0 + cbrt(1.0 + Re * t.Pr) * fRe;
+        double Sh, Nu;
+        if (Re * fmax(t.Sc, t.Pr) <= 0.015625) {
+            Sh = 2.0 + cbrt1p_small(Re * t.Sc);
+            Nu = 2.0 + cbrt1p_small(Re * t.Pr);
+        } else {
+            const double fRe = Re > 1.0 ? pow(Re, 0.077) : 1.0;
+            Sh = 1.0 + cbrt(1.0 + Re * t.Sc) * fRe;
+            Nu = 1.0 + cbrt(1.0 + Re * t.Pr) * fRe;
+        }
         a = D0 * (1.0 + KnM) * Sh * 0.5;
         b = K0 * (1.0 + KnT) * Nu * 0.5;
     }
@@ -150,27 +173,12 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
 }
 
 SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, int physics) {
-    const double r = sqrt(x);
-    const double rinv = 1.0 / r;
-    const double r3 = x * r;
+    const double rinv = rsqrt_hd(x);
+    const double r3 = x * x * rinv;
     const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
     const double kel = exp(t.A * rinv);
     const Coef c = growth_coef(rinv, r3, t, physics);
     return c.n * (t.rho_v_eff * den - t.rho_vs * num * kel) / (c.d * den);
-}
-
-// g(x0) for the bracket and the Euler step: the difference rho_v - rho_o,
-// where all the cancellation is, takes the operations of growth() one by
-// one; the factor 2 D_eff / rho_w, which only scales it, comes from
-// growth_coef (it differs from growth()'s by rounding, a relative 1e-16 of
-// g, which moves the Euler step by a relative 1e-16 of its increment)
-SDM_HD double growth_g0(double x, double rd3, double kappa, const Thermo &t, int physics) {
-    const double r = sqrt(x);
-    const double r3 = x * r;
-    const double aw = (r3 - rd3) / (r3 - rd3 * (1.0 - kappa));
-    const double rho_o = t.rho_vs * aw * exp(t.A / r);
-    const Coef c = growth_coef(1.0 / r, r3, t, physics);
-    return c.n / c.d * (t.rho_v_eff - rho_o);
 }
 
 // The FP32 growth rate with its error bound and dg/dx.
@@ -198,20 +206,54 @@ SDM_HD __noinline__ double fres_rare(double x, double x0, double rd3, double kap
     return fres(x, x0, rd3, kappa, *t, dtp, physics);
 }
 
-SDM_HD double fres_fast(double x, double x0, double rd3, double kappa, const Thermo &t, double dtp,
-                        int physics) {
-    return x - x0 - dtp * growth_fast(x, rd3, kappa, t, physics);
+// The fast solve's state between its FP64 growth evaluations (g(x0) first,
+// then one per polish step); solve_rw2_fast drives it.
+struct FastSolve {
+    double x0, rd3, kappa;
+    double a, b, lo, hi, xk, xp, fp, slope, sdx, sdf, x1;
+    float Lu, Hu, mu;
+    int k;
+    bool plo, undecided, mu_inside, pmu, have_slope;
+};
+
+// g(x0) for the bracket and the Euler step: rho_v - rho_o, where all the
+// cancellation is, takes the operations of growth() one by one; the factor
+// 2 D_eff / rho_w, which only scales it, comes from growth_coef (it differs
+// from growth()'s by rounding, a relative 1e-16 of g, which moves the Euler
+// step by a relative 1e-16 of its increment)
+SDM_HD double growth_g0(double x, double rd3, double kappa, const Thermo &t, int physics) {
+    const double r = sqrt(x);
+    const double r3 = x * r;
+    const double aw = (r3 - rd3) / (r3 - rd3 * (1.0 - kappa));
+    const double rho_o = t.rho_vs * aw * exp(t.A / r);
+    const Coef c = growth_coef(1.0 / r, r3, t, physics);
+    return c.n / c.d * (t.rho_v_eff - rho_o);
 }
 
-__host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
-                                          const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
-    // g(x0) sets the bracket and, when the bracket is ill-posed, the result
-    // itself, where its rounding is not damped by the stiffness of the
-    // implicit equation: its rho_v - rho_o is formed as growth() forms it
-    const double g0 = growth_g0(x0, rd3, kappa, t, physics);
-    const double a = fmax(rd2_of(rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
+// the exact bisection from [lo, hi] (FP64 signs, as the paper's bisection
+// takes them): for a polish that does not settle or a replay that leaves r
+SDM_HD __noinline__ double bisect_rest(double lo, double hi, bool plo, double x0, double rd3, double kappa,
+                                       const Thermo &t, double dtp, int physics) {
+    for (int it = 0; it < 200; ++it) {
+        if (hi - lo <= 0x1p-52 * hi) break;
+        const double m = 0.5 * (lo + hi);
+        if (!(m > lo && m < hi)) break;
+        if ((fres_rare(m, x0, rd3, kappa, &t, dtp, physics) > 0.0) == plo) lo = m;
+        else hi = m;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// After g0 = g(x0): bracket, ends, Euler step, locate.  Returns true when
+// the solve is finished (S.x1 set); otherwise S.xk is the first polish point.
+SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                        SolveCounters &cnt) {
+    const double x0 = S.x0;
+    const double a = fmax(rd2_of(S.rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
-    const float rd3f = (float)rd3, kf = (float)kappa, dtpf = (float)dtp, x0f = (float)x0;
+    S.a = a;
+    S.b = b;
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
     // 1. ends and locate.  The sign of f at x0 + d (d an FP32 increment) is
     //    computed in FP32 and trusted where |f| exceeds its error bound (it
     //    is then the sign an FP64 evaluation gives).  Points k = 0, 1 are the
@@ -239,7 +281,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
             p = f > 0.0f;
             if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
                 if (k < 2) {
-                    p = fres_rare(xe, x0, rd3, kappa, &t, dtp, physics) > 0.0;
+                    p = fres_rare(xe, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
                 } else {
                     mu = d;
                     undecided = true;
@@ -252,56 +294,126 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         } else if (k == 1) {
             if (pa == p) {  // f keeps its strict sign: the Euler step
                 cnt.euler++;
-                return 0.5 * (a + b);
+                S.x1 = 0.5 * (a + b);
+                return true;
             }
             plo = pa;
-            if (b - a <= 0x1p-52 * b) return 0.5 * (a + b);  // the bisection's own first exit
+            if (b - a <= 0x1p-52 * b) {  // the bisection's own first exit
+                S.x1 = 0.5 * (a + b);
+                return true;
+            }
         } else if (p == plo) {
             L = d;
         } else {
             H = d;
         }
     }
-    const float Lu = L, Hu = H;
+    S.plo = plo;
+    S.undecided = undecided;
+    S.Lu = L;
+    S.Hu = H;
     if (!undecided) mu = 0.5f * (L + H);
-    // 2. polish in FP64 inside [lo, hi], keeping the bracket with exact signs
+    S.mu = mu;
+    // 2. the polish starts at mu inside [lo, hi]
     double lo = x0 + (double)L, hi = x0 + (double)H;
     if (!(lo >= a)) lo = a;
     if (!(hi <= b)) hi = b;
     double xk = x0 + (double)mu;
-    const bool mu_inside = xk > lo && xk < hi;
-    if (!mu_inside) xk = 0.5 * (lo + hi);
-    bool pmu = false;  // the FP64 sign at mu, needed by the replay
-    double xp = 0.0, fp = 0.0, slope = 1.0 - dtp * (double)dg_last, r = 0.0;
-    double sdx = 1.0, sdf = 1.0;  // the last secant's steps
-    bool settled = false, have_slope = true;  // else the slope is sdf / sdx
-    for (int k = 0; k < 13; ++k) {
-        const double fk = fres_fast(xk, x0, rd3, kappa, t, dtp, physics);
-        if (k == 0) pmu = fk > 0.0;
-        if (fk == 0.0) {
-            r = xk;
-            settled = true;
-            break;
+    S.mu_inside = xk > lo && xk < hi;
+    if (!S.mu_inside) xk = 0.5 * (lo + hi);
+    S.lo = lo;
+    S.hi = hi;
+    S.xk = xk;
+    S.xp = S.fp = 0.0;
+    S.slope = 1.0 - dtp * (double)dg_last;  // Newton with the FP32 derivative first
+    S.sdx = S.sdf = 1.0;
+    S.have_slope = true;
+    S.pmu = false;
+    S.k = 0;
+    return false;
+}
+
+// 3. replay: near activation f need not be monotonic, and a bracket can hold
+//    several roots.  The polish found the one nearest mu; the bisection takes
+//    the one its halvings lead to.  Replaying those halvings from the bracket
+//    where FP32 stopped deciding (in FP32, and in FP64 wherever FP32 cannot
+//    tell away from r) checks that they lead to r; where they leave it, the
+//    exact bisection takes over.  Returns the solve's result.
+SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                        SolveCounters &cnt) {
+    const double x0 = S.x0;
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
+    // dr carries r - x0 to FP32: points within a few of its ulps are taken
+    // as r itself
+    const float dr = (float)(r - x0);
+    const float dtol = 4.0f * 5.9604645e-8f * fabsf(dr);
+    const bool plo = S.plo;
+    float RL = S.Lu, RH = S.Hu;
+    if (S.mu_inside) {
+        if (!(fabsf(S.mu - dr) <= dtol || (S.pmu == plo) == (S.mu < dr))) {
+            cnt.fallback++;
+            return bisect_rest(S.pmu == plo ? fmax(S.a, x0 + (double)S.mu) : fmax(S.a, x0 + (double)RL),
+                               S.pmu == plo ? fmin(S.b, x0 + (double)RH) : fmin(S.b, x0 + (double)S.mu), plo,
+                               x0, S.rd3, S.kappa, t, dtp, physics);
         }
-        if ((fk > 0.0) == plo) lo = xk;
-        else hi = xk;
-        if (hi - lo <= 0x1p-46 * hi) {
-            r = 0.5 * (lo + hi);
-            settled = true;
-            break;
+        if (S.pmu == plo) RL = S.mu;
+        else RH = S.mu;
+    }
+    for (int it = 0; it < 64; ++it) {
+        const float m = 0.5f * (RL + RH);
+        if (!(m > RL && m < RH) || fabsf(m - dr) <= dtol) break;
+        const GF q = growth_f3_call(x0f + m, rd3f, kf, &tf, physics);
+        const float f = m - dtpf * q.g, nz = 2.4e-7f * fabsf(m) + 4.0f * dtpf * q.err;
+        bool pm = f > 0.0f;
+        if (!(fabsf(f) > nz)) {
+            // within a few noise widths of r: the halvings close in on r
+            const double sl = fabs(S.have_slope ? S.slope : S.sdf / S.sdx);
+            if ((double)fabsf(m - dr) * sl <= 8.0 * (double)nz) break;
+            pm = fres_rare(x0 + (double)m, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
         }
-        if (k == 12) break;
-        // Newton with the FP32 derivative of the last FP32 evaluation first,
-        // then secant steps
-        const bool secant = k > 0 && fk != fp;
+        if (pm == plo) RL = m;
+        else RH = m;
+        if (pm != (plo == (m < dr))) {
+            cnt.fallback++;
+            return bisect_rest(fmax(S.a, x0 + (double)RL), fmin(S.b, x0 + (double)RH), plo, x0, S.rd3, S.kappa,
+                               t, dtp, physics);
+        }
+    }
+    return r;
+}
+
+// After v = growth_fast(S.xk): one polish step (bracketed Newton, then
+// secant, in FP64 with exact signs).  Returns true when the solve is
+// finished (S.x1 set).
+SDM_HD bool fs_after_polish(FastSolve &S, double v, const Thermo &t, const ThermoF &tf, double dtp,
+                            int physics, SolveCounters &cnt) {
+    const double xk = S.xk, fk = xk - S.x0 - dtp * v;
+    const int k = S.k;
+    if (k == 0) S.pmu = fk > 0.0;
+    double r = 0.0;
+    bool settled = false;
+    if (fk == 0.0) {
+        r = xk;
+        settled = true;
+    } else {
+        if ((fk > 0.0) == S.plo) S.lo = xk;
+        else S.hi = xk;
+        if (S.hi - S.lo <= 0x1p-46 * S.hi) {
+            r = 0.5 * (S.lo + S.hi);
+            settled = true;
+        }
+    }
+    if (!settled && k < 12) {
+        const double lo = S.lo, hi = S.hi;
+        const bool secant = k > 0 && fk != S.fp;
         double xn;
         if (secant) {
-            sdx = xk - xp;
-            sdf = fk - fp;
-            xn = xk - fk * (sdx / sdf);
-            have_slope = false;
+            S.sdx = xk - S.xp;
+            S.sdf = fk - S.fp;
+            xn = xk - fk * (S.sdx / S.sdf);
+            S.have_slope = false;
         } else {
-            xn = slope != 0.0 ? xk - fk / slope : 0.5 * (lo + hi);
+            xn = S.slope != 0.0 ? xk - fk / S.slope : 0.5 * (lo + hi);
         }
         // a step past an end of the bracket says the root hugs that end
         bool clamped = false;
@@ -320,69 +432,34 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         if (!clamped && fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk) {
             r = xn;
             settled = true;
-            break;
+        } else {
+            S.xp = xk;
+            S.fp = fk;
+            S.xk = xn;
+            S.k = k + 1;
+            return false;
         }
-        xp = xk;
-        fp = fk;
-        xk = xn;
     }
-    // 3. replay: near activation f need not be monotonic, and a bracket can
-    //    hold several roots.  The polish found the one nearest mu; the
-    //    bisection takes the one its halvings lead to.  Replaying those
-    //    halvings from the bracket where FP32 stopped deciding (in FP32, and
-    //    in FP64 wherever FP32 cannot tell away from r) checks that they lead
-    //    to r; where they leave it, the exact bisection takes over.
-    if (settled && undecided) {
-        // dr carries r - x0 to FP32: points within a few of its ulps are
-        // taken as r itself
-        const float dr = (float)(r - x0);
-        const float dtol = 4.0f * 5.9604645e-8f * fabsf(dr);
-        float RL = Lu, RH = Hu;
-        bool consistent = true;
-        if (mu_inside) {
-            consistent = fabsf(mu - dr) <= dtol || (pmu == plo) == (mu < dr);
-            if (pmu == plo) RL = mu;
-            else RH = mu;
-        }
-        for (int it = 0; it < 64 && consistent; ++it) {
-            const float m = 0.5f * (RL + RH);
-            if (!(m > RL && m < RH) || fabsf(m - dr) <= dtol) break;
-            const GF q = growth_f3_call(x0f + m, rd3f, kf, &tf, physics);
-            const float f = m - dtpf * q.g, nz = 2.4e-7f * fabsf(m) + 4.0f * dtpf * q.err;
-            bool pm = f > 0.0f;
-            if (!(fabsf(f) > nz)) {
-                // within a few noise widths of r: the halvings close in on r
-                const double sl = fabs(have_slope ? slope : sdf / sdx);
-                if ((double)fabsf(m - dr) * sl <= 8.0 * (double)nz) break;
-                pm = fres_rare(x0 + (double)m, x0, rd3, kappa, &t, dtp, physics) > 0.0;
-            }
-            if (pm != (plo == (m < dr))) {
-                consistent = false;
-                // continue the exact bisection from this halving's bracket
-                if (pm == plo) RL = m;
-                else RH = m;
-                lo = fmax(a, x0 + (double)RL);
-                hi = fmin(b, x0 + (double)RH);
-                break;
-            }
-            if (pm == plo) RL = m;
-            else RH = m;
-        }
-        if (consistent) return r;
-    } else if (settled) {
-        return r;
+    if (!settled) {  // did not settle in 13 evaluations
+        cnt.fallback++;
+        S.x1 = bisect_rest(S.lo, S.hi, S.plo, S.x0, S.rd3, S.kappa, t, dtp, physics);
+        return true;
     }
-    // did not settle, or the replay left r: the exact bisection in the
-    // current bracket (FP64 signs, as the paper's bisection takes them)
-    cnt.fallback++;
-    for (int it = 0; it < 200; ++it) {
-        if (hi - lo <= 0x1p-52 * hi) break;
-        const double m = 0.5 * (lo + hi);
-        if (!(m > lo && m < hi)) break;
-        if ((fres_rare(m, x0, rd3, kappa, &t, dtp, physics) > 0.0) == plo) lo = m;
-        else hi = m;
-    }
-    return 0.5 * (lo + hi);
+    S.x1 = S.undecided ? fs_replay(S, r, t, tf, dtp, physics, cnt) : r;
+    return true;
+}
+
+// the whole fast solve for one super-droplet
+__host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
+                                          const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
+    FastSolve S;
+    S.x0 = x0;
+    S.rd3 = rd3;
+    S.kappa = kappa;
+    if (fs_after_g0(S, growth_g0(x0, rd3, kappa, t, physics), t, tf, dtp, physics, cnt)) return S.x1;
+    for (int k = 0; k < 13; ++k)
+        if (fs_after_polish(S, growth_fast(S.xk, rd3, kappa, t, physics), t, tf, dtp, physics, cnt)) return S.x1;
+    return S.x1;  // not reached: the polish finishes within 13 evaluations
 }
 
 // ---------------------------------------------------------------------------
@@ -450,11 +527,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// LPC lanes per cell (a power of two <= 32): each lane solves every LPC-th
+// LPC lanes per cell (4, 8 or 32): each lane solves every LPC-th
 // super-droplet of its cell, the group's lanes share the cell's
-// thermodynamics and sum through shuffles inside the group.  Fewer lanes per
-// cell give each lane more super-droplets, which evens out the solve's
-// data-dependent cost across the warp.
+// thermodynamics and sum through shuffles inside the group.
 // MODE: the solver, fixed at compile time so that each kernel carries only
 // its own code.
 enum { kModeBisect = 0, kModeFast = 1, kModeMixed = 2 };
@@ -478,7 +553,7 @@ __device__ __forceinline__ double solve_mode(double x0, double rd3, double kappa
 constexpr int kMaxBlock = 128;
 
 template <int LPC, int MODE>
-__global__ void __launch_bounds__(kMaxBlock, 5) k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
+__global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
                            const double *rhod, Grid g, int sstp, double RH_max, int physics, DevStats *st) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -590,6 +665,17 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
         if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
         if (anybad) atomicOr(&st->flags, kFlagNumeric);
     }
+}
+
+// the largest block the ensemble condensation kernel of this mode launches
+// with (its register count bounds it)
+int ens_cond_max_threads(const EnsCondParams &p) {
+    cudaFuncAttributes a{};
+    cudaError_t e;
+    if (p.mixed) e = cudaFuncGetAttributes(&a, k_ens_cond_tiles<kModeMixed>);
+    else if (p.solver == 0) e = cudaFuncGetAttributes(&a, k_ens_cond_tiles<kModeBisect>);
+    else e = cudaFuncGetAttributes(&a, k_ens_cond_tiles<kModeFast>);
+    return e == cudaSuccess ? a.maxThreadsPerBlock : 128;
 }
 
 cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,

@@ -83,6 +83,16 @@ struct Thermo {
     double rho_a, nu, lambda_D, lambda_K, Sc, Pr, cX;
 };
 
+// 1 / sqrt(x): the device's reciprocal square root (host builds, used by
+// test harnesses, divide)
+SDM_HD double rsqrt_hd(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
 // (rho_d R_d / p1000)^(R_d / c_pd): the rho_d factor of T in Appendix A,
 // constant over a step (rho_d changes only between steps)
 SDM_HD double rhod_factor(double rhod) {
@@ -91,10 +101,13 @@ SDM_HD double rhod_factor(double rhod) {
 }
 
 // Appendix A: T and p from theta, r_v, rho_d; Sec. 5.1.3 quantities.
-// fast_mu: the viscosity's (T/273)^1.5 as x sqrt(x) rather than pow; mu
-// only scales D_eff's ventilation terms, so the condensation kernels take
-// it (the coalescence ambient keeps pow).
-template <bool fast_mu = false>
+// cond = true (the condensation kernels): T, rho_vs, A and dtheta/dr_v take
+// exactly the operations below, since the growth rate's cancellation and the
+// theta update depend on their last bits; the air's transport properties
+// (mu, nu, lambda_D, lambda_K, Sc, Pr, c_X) and Dterm, which only scale
+// D_eff, use reciprocals and x sqrt(x) for (T/273)^1.5 and so differ from
+// the cond = false values (the coalescence ambient) by rounding.
+template <bool cond = false>
 SDM_HD Thermo thermo_eval_f(double th, double rv, double rhod, double RH_max, double rhod_f) {
     using namespace phys;
     Thermo t;
@@ -103,24 +116,38 @@ SDM_HD Thermo thermo_eval_f(double th, double rv, double rhod, double RH_max, do
     t.rhod = rhod;
     t.T = pow(th * rhod_f, c_pd / (c_pd - R_d));
     t.lv = l_v0 + (c_pv - c_l) * (t.T - T0);
+    const double rT = 1.0 / t.T;
     // Clausius-Clapeyron integrated with the linear l_v(T)
-    const double lnp = (l_v0 + (c_l - c_pv) * T0) / R_v * (1.0 / T0 - 1.0 / t.T) -
+    const double lnp = (l_v0 + (c_l - c_pv) * T0) / R_v * (1.0 / T0 - rT) -
                        (c_l - c_pv) / R_v * log(t.T / T0);
     t.rho_vs = p_vs0 * exp(lnp) / (R_v * t.T);
     t.rho_v = rv * rhod;
     t.rho_v_eff = fmin(t.rho_v, RH_max * t.rho_vs);
     t.dth_drv = -th * t.lv / (c_pd * t.T);
     t.A = 2.0 * sigma_w / (R_v * t.T * rho_w);
-    t.Dterm = t.rho_vs * t.lv / t.T * (t.lv / (R_v * t.T) - 1.0);
     t.rho_a = rhod * (1.0 + rv);
     const double Tr = t.T / 273.0;
-    const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * (fast_mu ? Tr * sqrt(Tr) : pow(Tr, 1.5));
-    t.nu = mu / t.rho_a;
-    t.lambda_D = 2.0 * D0 / sqrt(8.0 * R_v * t.T / pi);
-    t.lambda_K = 2.0 * K0 / (t.rho_a * c_pd * sqrt(8.0 * R_d * t.T / pi));
-    t.Sc = t.nu / D0;
-    t.Pr = t.nu * t.rho_a * c_pd / K0;
-    t.cX = 32.0 / 3.0 * (rho_w - t.rho_a) / t.rho_a * grav / (t.nu * t.nu);
+    if (cond) {
+        t.Dterm = t.rho_vs * t.lv * rT * (t.lv * rT * (1.0 / R_v) - 1.0);
+        const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * (Tr * sqrt(Tr));
+        const double ra = 1.0 / t.rho_a;
+        t.nu = mu * ra;
+        t.lambda_D = 2.0 * D0 * rsqrt_hd(8.0 / pi * R_v * t.T);
+        t.lambda_K = 2.0 * K0 / c_pd * ra * rsqrt_hd(8.0 / pi * R_d * t.T);
+        t.Sc = t.nu * (1.0 / D0);
+        t.Pr = t.nu * t.rho_a * (c_pd / K0);
+        const double rnu = 1.0 / t.nu;
+        t.cX = 32.0 / 3.0 * grav * (rho_w - t.rho_a) * ra * (rnu * rnu);
+    } else {
+        t.Dterm = t.rho_vs * t.lv / t.T * (t.lv / (R_v * t.T) - 1.0);
+        const double mu = 1.72e-5 * (393.0 / (t.T + 120.0)) * pow(Tr, 1.5);
+        t.nu = mu / t.rho_a;
+        t.lambda_D = 2.0 * D0 / sqrt(8.0 * R_v * t.T / pi);
+        t.lambda_K = 2.0 * K0 / (t.rho_a * c_pd * sqrt(8.0 * R_d * t.T / pi));
+        t.Sc = t.nu / D0;
+        t.Pr = t.nu * t.rho_a * c_pd / K0;
+        t.cX = 32.0 / 3.0 * (rho_w - t.rho_a) / t.rho_a * grav / (t.nu * t.nu);
+    }
     return t;
 }
 
@@ -304,6 +331,9 @@ struct EnsCondParams {
     int sstp, physics, solver, mixed;
     double RH_max;
 };
+
+// the largest block k_ens_cond_tiles launches with for these parameters
+int ens_cond_max_threads(const EnsCondParams &p);
 
 // one substep of condensation for every tile (k_cond.cu)
 cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t *tile_member,

@@ -166,3 +166,40 @@ def test_parcel_keeps_dry_air_mass():
     assert m1 == pytest.approx(m0, rel=1e-3)
     th, rv = ens.fields([mid])
     assert rv[0] < 8.0e-3  # the rising parcel condenses
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_state_and_picks_a_launchable_shape(precision):
+    """The autotuner times condensation tile/block shapes on the resident
+    state: it must leave that state and the counters as they were, skip the
+    block sizes the kernel's register count rules out, and leave the
+    ensemble stepping as before (two ensembles, one tuned, stay within the
+    rounding of a different tile split)."""
+    ms = [member(n, s) for n, s in ((30000, 21), (700, 22), (120000, 23))]
+    tuned, plain = (Ensemble(precision=precision, max_sd=1 << 18, max_members=4) for _ in range(2))
+    tid = [tuned.add(m) for m in ms]
+    pid = [plain.add(m) for m in ms]
+    for e in (tuned, plain):
+        e.step(ALL0D)
+        e.wait()
+    before = [state(tuned, i, m["n_sd"]) for i, m in zip(tid, ms)]
+    stats_before = tuned.stats()
+    tile, threads = tuned.autotune(ALL0D)
+    assert tile in (128, 256, 512, 1024, 2048) and threads in (128, 256, 512)
+    after = [state(tuned, i, m["n_sd"]) for i, m in zip(tid, ms)]
+    for b, a in zip(before, after):
+        for k in b:
+            assert np.array_equal(b[k], a[k]), k
+    assert tuned.stats() == stats_before
+    for _ in range(3):
+        for e in (tuned, plain):
+            e.step(ALL0D)
+            e.wait()
+    for i, j, m in zip(tid, pid, ms):
+        a, b = state(tuned, i, m["n_sd"]), state(plain, j, m["n_sd"])
+        assert np.isfinite(a["rw2"]).all()
+        if precision == "fp64":  # FP32 accept decisions may flip under rounding changes
+            assert np.array_equal(a["N"], b["N"])
+            # another tile split rounds the member sums differently; activating
+            # droplets amplify that (up to ~1e-11 per ulp of the ambient state)
+            np.testing.assert_allclose(a["rw2"], b["rw2"], rtol=1e-9)
