@@ -72,10 +72,14 @@ SDM_HD float fs_f(float Kn) {
     return (1.0f + Kn) / (1.0f + (4.0f / 3.0f + 0.377f) * Kn + 4.0f / 3.0f * Kn * Kn);
 }
 
-// FP32 growth rate g, an absolute error bound for it, and (optionally) an
-// approximate derivative dg/dx that ignores the slow variation of D_eff.
-SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t,
-                                          int physics, float *err, float *dgdx) {
+// FP32 growth rate g and an absolute error bound for it; with DG > 0 also
+// its derivative dg/dx: DG = 1 through the Koehler factor only, DG = 2 also
+// through D_eff's variation with r (transition regime and ventilation), for
+// the polish's first Newton step.
+enum { kDgNone = 0, kDgKoehler = 1, kDgFull = 2 };
+
+template <int DG>
+SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int physics, float *err, float *dgdx) {
     const float r = sqrtf(x);
     const float r3 = x * r;
     const float num = r3 - rd3, den = r3 - rd3 * (1.0f - kappa);
@@ -84,16 +88,35 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t,
     const float kel = expf(Ar);
     const float rho_o = t.rho_vs * aw * kel;
     float D = (float)phys::D0, K = (float)phys::K0;
+    float dlnD = 0.0f, dlnK = 0.0f;  // d ln D / d ln r, d ln K / d ln r
     if (physics) {
-        const float bM = fs_f(t.lambda_D / r), bT = fs_f(t.lambda_K / r);
+        const float c1 = 4.0f / 3.0f + 0.377f, c2 = 4.0f / 3.0f;
+        const float KnM = t.lambda_D / r, KnT = t.lambda_K / r;
+        const float bM = fs_f(KnM), bT = fs_f(KnT);
         const float X = t.cX * r3;
-        const float c1 = (float)(4.0 / (phys::delta0 * phys::delta0 * 0.54037024344425184));  // sqrt(C0)
-        const float e = c1 * sqrtf(X);
-        const float s = e / (sqrtf(1.0f + e) + 1.0f);
+        const float ce = (float)(4.0 / (phys::delta0 * phys::delta0 * 0.54037024344425184));  // sqrt(C0)
+        const float e = ce * sqrtf(X);
+        const float sq = sqrtf(1.0f + e);
+        const float s = e / (sq + 1.0f);
         const float Re = (float)(phys::delta0 * phys::delta0 / 4.0) * s * s;
         const float fRe = Re > 1.0f ? powf(Re, 0.077f) : 1.0f;
-        D = (float)phys::D0 * bM * (1.0f + cbrtf(1.0f + Re * t.Sc) * fRe) * 0.5f;
-        K = (float)phys::K0 * bT * (1.0f + cbrtf(1.0f + Re * t.Pr) * fRe) * 0.5f;
+        const float qS = cbrtf(1.0f + Re * t.Sc), qP = cbrtf(1.0f + Re * t.Pr);
+        const float Sh = 1.0f + qS * fRe, Nu = 1.0f + qP * fRe;
+        D = (float)phys::D0 * bM * Sh * 0.5f;
+        K = (float)phys::K0 * bT * Nu * 0.5f;
+        if (DG == kDgFull) {
+            // d ln beta / d ln r = -d ln beta / d ln Kn
+            auto dlnbeta = [&](float Kn) {
+                return (c1 * Kn + 2.0f * c2 * Kn * Kn) / (1.0f + c1 * Kn + c2 * Kn * Kn) - Kn / (1.0f + Kn);
+            };
+            // Re(X), X ~ r^3: d ln Re / d ln r = 3 e / (2 s sqrt(1 + e))
+            const float dlnRe = s > 0.0f ? 3.0f * e / (2.0f * s * sq) : 3.0f;
+            const float dfRe = Re > 1.0f ? 0.077f : 0.0f;  // d ln fRe / d ln Re
+            const float dSh = fRe * (Re * t.Sc / (3.0f * qS * qS) + dfRe * qS) * dlnRe / Sh;
+            const float dNu = fRe * (Re * t.Pr / (3.0f * qP * qP) + dfRe * qP) * dlnRe / Nu;
+            dlnD = dlnbeta(KnM) + dSh;
+            dlnK = dlnbeta(KnT) + dNu;
+        }
     }
     const float Deff = 1.0f / (1.0f / D + t.Dterm / K);
     const float c = 2.0f * Deff / (float)phys::rho_w;
@@ -103,9 +126,12 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t,
     const float amp = (r3 + rd3) / fmaxf(fabsf(num), 1e-37f);
     const float eps = 5.9604645e-8f;  // 2^-24
     *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 4.0f * Ar)) + 64.0f * fabsf(g));
-    if (dgdx) {
+    if (DG != kDgNone) {
         const float drho_dr = t.rho_vs * kel * (3.0f * r * r * rd3 * kappa / (den * den) - aw * t.A / (r * r));
-        *dgdx = -c * drho_dr / (2.0f * r);
+        // D_eff = 1 / (1/D + Dterm/K): d ln D_eff = (D_eff/D) d ln D + (1 - D_eff/D) d ln K
+        const float wD = Deff / D;
+        const float dlnc = wD * dlnD + (1.0f - wD) * dlnK;
+        *dgdx = (g * dlnc - c * drho_dr * r) / (2.0f * x);
     }
     return g;
 }
@@ -172,23 +198,16 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
     return Coef{2.0 * a * b, rho_w * (b * DM + t.Dterm * a * DT)};
 }
 
-SDM_HD double growth_fast(double x, double rd3, double kappa, const Thermo &t, int physics) {
-    const double rinv = rsqrt_hd(x);
-    const double r3 = x * x * rinv;
-    const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
-    const double kel = exp(t.A * rinv);
-    const Coef c = growth_coef(rinv, r3, t, physics);
-    return c.n * (t.rho_v_eff * den - t.rho_vs * num * kel) / (c.d * den);
-}
-
 // The FP32 growth rate with its error bound and dg/dx.
 struct GF {
     float g, err, dg;
 };
 
+template <int DG>
 SDM_HD GF growth_f3(float x, float rd3, float kappa, const ThermoF &t, int physics) {
     GF r;
-    r.g = growth_f(x, rd3, kappa, t, physics, &r.err, &r.dg);
+    r.dg = 0.0f;
+    r.g = growth_f<DG>(x, rd3, kappa, t, physics, &r.err, &r.dg);
     return r;
 }
 
@@ -196,7 +215,11 @@ SDM_HD GF growth_f3(float x, float rd3, float kappa, const ThermoF &t, int physi
 // hot code small (their main stall is instruction fetch); the ambient
 // state is passed by address (it lives in shared memory in the kernels).
 SDM_HD __noinline__ GF growth_f3_call(float x, float rd3, float kappa, const ThermoF *t, int physics) {
-    return growth_f3(x, rd3, kappa, *t, physics);
+    return growth_f3<kDgNone>(x, rd3, kappa, *t, physics);
+}
+
+SDM_HD __noinline__ GF growth_f3_full(float x, float rd3, float kappa, const ThermoF *t, int physics) {
+    return growth_f3<kDgFull>(x, rd3, kappa, *t, physics);
 }
 
 // the FP64 residual with the term-by-term growth rate, on the rare paths
@@ -216,18 +239,37 @@ struct FastSolve {
     bool plo, undecided, mu_inside, pmu, have_slope;
 };
 
-// g(x0) for the bracket and the Euler step: rho_v - rho_o, where all the
-// cancellation is, takes the operations of growth() one by one; the factor
-// 2 D_eff / rho_w, which only scales it, comes from growth_coef (it differs
-// from growth()'s by rounding, a relative 1e-16 of g, which moves the Euler
-// step by a relative 1e-16 of its increment)
-SDM_HD double growth_g0(double x, double rd3, double kappa, const Thermo &t, int physics) {
-    const double r = sqrt(x);
+// The growth rate for the fast solve, one evaluation for both of its uses
+// so that the solve has one copy of it.
+// exact = true: g(x0) for the bracket and the Euler step.  rho_v - rho_o,
+//   where all the cancellation is, takes the operations of growth() one by
+//   one; the factor 2 D_eff / rho_w, which only scales it, comes from
+//   growth_coef (it differs from growth()'s by rounding, a relative 1e-16 of
+//   g, which moves the Euler step by a relative 1e-16 of its increment).
+// exact = false: the one-division form above (the polish), and in *mag the
+//   same factor times rho_v + rho_o, the size of the terms whose difference
+//   g is (its rounding error is a few ulps of this).
+SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const Thermo &t, int physics,
+                          double *mag) {
+    double r, rinv;
+    if (exact) {
+        r = sqrt(x);
+        rinv = 1.0 / r;
+    } else {
+        rinv = rsqrt_hd(x);
+        r = x * rinv;
+    }
     const double r3 = x * r;
-    const double aw = (r3 - rd3) / (r3 - rd3 * (1.0 - kappa));
-    const double rho_o = t.rho_vs * aw * exp(t.A / r);
-    const Coef c = growth_coef(1.0 / r, r3, t, physics);
-    return c.n / c.d * (t.rho_v_eff - rho_o);
+    const double kel = exp(exact ? t.A / r : t.A * rinv);
+    const Coef c = growth_coef(rinv, r3, t, physics);
+    const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
+    if (exact) {
+        *mag = 0.0;
+        return c.n / c.d * (t.rho_v_eff - t.rho_vs * (num / den) * kel);
+    }
+    const double q = c.n / (c.d * den), v = t.rho_v_eff * den, o = t.rho_vs * num * kel;
+    *mag = q * (v + fabs(o));
+    return q * (v - o);
 }
 
 // the exact bisection from [lo, hi] (FP64 signs, as the paper's bisection
@@ -275,9 +317,8 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
         if (k < 2 && xe == x0) {
             p = -dtp * g0 > 0.0;
         } else {
-            const GF q = growth_f3(x0f + d, rd3f, kf, tf, physics);
+            const GF q = growth_f3<kDgNone>(x0f + d, rd3f, kf, tf, physics);
             const float f = d - dtpf * q.g;
-            dg_last = q.dg;
             p = f > 0.0f;
             if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
                 if (k < 2) {
@@ -314,6 +355,8 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     S.Hu = H;
     if (!undecided) mu = 0.5f * (L + H);
     S.mu = mu;
+    // f' at mu for the first Newton step (D_eff's variation included)
+    dg_last = growth_f3_full(x0f + mu, rd3f, kf, &tf, physics).dg;
     // 2. the polish starts at mu inside [lo, hi]
     double lo = x0 + (double)L, hi = x0 + (double)H;
     if (!(lo >= a)) lo = a;
@@ -343,10 +386,11 @@ SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &
                         SolveCounters &cnt) {
     const double x0 = S.x0;
     const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
-    // dr carries r - x0 to FP32: points within a few of its ulps are taken
-    // as r itself
+    // dr carries r - x0 to FP32: points within a few of its ulps, or within a
+    // few FP64 ulps of r itself (the signs are taken at FP64 points), are
+    // taken as r
     const float dr = (float)(r - x0);
-    const float dtol = 4.0f * 5.9604645e-8f * fabsf(dr);
+    const float dtol = fmaxf(4.0f * 5.9604645e-8f * fabsf(dr), (float)(0x1p-50 * r));
     const bool plo = S.plo;
     float RL = S.Lu, RH = S.Hu;
     if (S.mu_inside) {
@@ -382,12 +426,14 @@ SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &
     return r;
 }
 
-// After v = growth_fast(S.xk): one polish step (bracketed Newton, then
-// secant, in FP64 with exact signs).  Returns true when the solve is
+// After v = growth_eval(S.xk, false, .., &mag): one polish step (bracketed
+// Newton, then secant, in FP64 with exact signs).  Returns true when the solve is
 // finished (S.x1 set).
-SDM_HD bool fs_after_polish(FastSolve &S, double v, const Thermo &t, const ThermoF &tf, double dtp,
+SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t, const ThermoF &tf, double dtp,
                             int physics, SolveCounters &cnt) {
     const double xk = S.xk, fk = xk - S.x0 - dtp * v;
+    // f(xk) within the rounding of its own evaluation (16 ulps of its terms)
+    const bool at_noise = fabs(fk) <= 0x1p-48 * (fabs(xk - S.x0) + dtp * mag);
     const int k = S.k;
     if (k == 0) S.pmu = fk > 0.0;
     double r = 0.0;
@@ -415,24 +461,22 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, const Thermo &t, const Therm
         } else {
             xn = S.slope != 0.0 ? xk - fk / S.slope : 0.5 * (lo + hi);
         }
-        // a step past an end of the bracket says the root hugs that end
-        bool clamped = false;
-        if (!(xn < hi)) {
-            xn = hi - (hi - lo) * 0.015625;
-            clamped = true;
-        }
-        if (!(xn > lo)) {
-            xn = lo + (hi - lo) * 0.015625;
-            clamped = true;
-        }
         // the secant converges superlinearly: once its step is below 2^-30 x
         // the error left is of order (2^-30)(previous step) x, far below
         // 2^-46 x; a Newton step with the approximate FP32 derivative must
-        // itself be that small
-        if (!clamped && fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk) {
+        // itself be that small.  A step onto the end of the bracket that xk
+        // has just become (a correction below one ulp) settles only when
+        // f(xk) is at the rounding level of its evaluation: near it a secant
+        // slope from close points is itself rounding.
+        const bool inside = at_noise ? xn >= lo && xn <= hi : xn > lo && xn < hi;
+        if (fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk && inside) {
             r = xn;
             settled = true;
         } else {
+            // a larger step past an end of the bracket says the root hugs that
+            // end: move 1/64 in from it
+            if (!(xn < hi)) xn = hi - (hi - lo) * 0.015625;
+            if (!(xn > lo)) xn = lo + (hi - lo) * 0.015625;
             S.xp = xk;
             S.fp = fk;
             S.xk = xn;
@@ -456,9 +500,14 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     S.x0 = x0;
     S.rd3 = rd3;
     S.kappa = kappa;
-    if (fs_after_g0(S, growth_g0(x0, rd3, kappa, t, physics), t, tf, dtp, physics, cnt)) return S.x1;
-    for (int k = 0; k < 13; ++k)
-        if (fs_after_polish(S, growth_fast(S.xk, rd3, kappa, t, physics), t, tf, dtp, physics, cnt)) return S.x1;
+    // g(x0), then one growth evaluation per polish step, through one call site
+    for (int k = 0; k < 14; ++k) {
+        const bool first = k == 0;
+        double mag;
+        const double v = growth_eval(first ? x0 : S.xk, first, rd3, kappa, t, physics, &mag);
+        if (first ? fs_after_g0(S, v, t, tf, dtp, physics, cnt) : fs_after_polish(S, v, mag, t, tf, dtp, physics, cnt))
+            return S.x1;
+    }
     return S.x1;  // not reached: the polish finishes within 13 evaluations
 }
 
@@ -476,7 +525,7 @@ __host__ __device__ bool solve_rw2_f32(double x0, double rd3, double kappa, cons
     const float lo_d = fmaxf((float)((double)(rdf * rdf) - x0), fminf(2.0f * dtp * g0, 0.0f));
     const float hi_d = fmaxf(2.0f * dtp * g0, 0.0f);
     auto f = [&](float d, float *der) -> float {
-        const GF q = growth_f3((float)(x0 + (double)d), rd3f, kf, tf, physics);
+        const GF q = growth_f3<kDgKoehler>((float)(x0 + (double)d), rd3f, kf, tf, physics);
         if (der) *der = 1.0f - dtp * q.dg;
         return d - dtp * q.g;
     };
