@@ -68,8 +68,20 @@ SDM_HD ThermoF to_float(const Thermo &t) {
     return f;
 }
 
+// a / b within 2 ulps (the device's fast division; exact on the host).  The
+// FP32 growth rate below uses it throughout: its error bound allows 16 ulps
+// of rho_o, 8 amp of a_w and 64 of the D_eff factor, so 2-ulp quotients stay
+// well inside it, and the fast form keeps the kernels' code small.
+SDM_HD float fdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
 SDM_HD float fs_f(float Kn) {
-    return (1.0f + Kn) / (1.0f + (4.0f / 3.0f + 0.377f) * Kn + 4.0f / 3.0f * Kn * Kn);
+    return fdiv(1.0f + Kn, 1.0f + (4.0f / 3.0f + 0.377f) * Kn + 4.0f / 3.0f * Kn * Kn);
 }
 
 // FP32 growth rate g and an absolute error bound for it; with DG > 0 also
@@ -83,21 +95,21 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
     const float r = sqrtf(x);
     const float r3 = x * r;
     const float num = r3 - rd3, den = r3 - rd3 * (1.0f - kappa);
-    const float aw = num / den;
-    const float Ar = t.A / r;
+    const float aw = fdiv(num, den);
+    const float Ar = fdiv(t.A, r);
     const float kel = expf(Ar);
     const float rho_o = t.rho_vs * aw * kel;
     float D = (float)phys::D0, K = (float)phys::K0;
     float dlnD = 0.0f, dlnK = 0.0f;  // d ln D / d ln r, d ln K / d ln r
     if (physics) {
         const float c1 = 4.0f / 3.0f + 0.377f, c2 = 4.0f / 3.0f;
-        const float KnM = t.lambda_D / r, KnT = t.lambda_K / r;
+        const float KnM = fdiv(t.lambda_D, r), KnT = fdiv(t.lambda_K, r);
         const float bM = fs_f(KnM), bT = fs_f(KnT);
         const float X = t.cX * r3;
         const float ce = (float)(4.0 / (phys::delta0 * phys::delta0 * 0.54037024344425184));  // sqrt(C0)
         const float e = ce * sqrtf(X);
         const float sq = sqrtf(1.0f + e);
-        const float s = e / (sq + 1.0f);
+        const float s = fdiv(e, sq + 1.0f);
         const float Re = (float)(phys::delta0 * phys::delta0 / 4.0) * s * s;
         const float fRe = Re > 1.0f ? powf(Re, 0.077f) : 1.0f;
         const float qS = cbrtf(1.0f + Re * t.Sc), qP = cbrtf(1.0f + Re * t.Pr);
@@ -118,12 +130,12 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
             dlnK = dlnbeta(KnT) + dNu;
         }
     }
-    const float Deff = 1.0f / (1.0f / D + t.Dterm / K);
+    const float Deff = fdiv(1.0f, fdiv(1.0f, D) + fdiv(t.Dterm, K));
     const float c = 2.0f * Deff / (float)phys::rho_w;
     const float g = c * (t.rho_v_eff - rho_o);
     // rounding of the difference's terms (a_w amplified where r ~ r_d) and
     // of the D_eff factor, with a safety factor
-    const float amp = (r3 + rd3) / fmaxf(fabsf(num), 1e-37f);
+    const float amp = fdiv(r3 + rd3, fmaxf(fabsf(num), 1e-37f));
     const float eps = 5.9604645e-8f;  // 2^-24
     *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 4.0f * Ar)) + 64.0f * fabsf(g));
     if (DG != kDgNone) {
@@ -211,9 +223,10 @@ SDM_HD GF growth_f3(float x, float rd3, float kappa, const ThermoF &t, int physi
     return r;
 }
 
-// Out-of-line copies for the less frequent call sites keep the kernels'
-// hot code small (their main stall is instruction fetch); the ambient
-// state is passed by address (it lives in shared memory in the kernels).
+// Out-of-line copies of the FP32 growth rate keep the kernels' hot code
+// small (their main stall is instruction fetch): one copy serves the locate
+// loop and the replay.  The ambient state is passed by address (it lives in
+// shared memory in the kernels).
 SDM_HD __noinline__ GF growth_f3_call(float x, float rd3, float kappa, const ThermoF *t, int physics) {
     return growth_f3<kDgNone>(x, rd3, kappa, *t, physics);
 }
@@ -317,7 +330,7 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
         if (k < 2 && xe == x0) {
             p = -dtp * g0 > 0.0;
         } else {
-            const GF q = growth_f3<kDgNone>(x0f + d, rd3f, kf, tf, physics);
+            const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
             const float f = d - dtpf * q.g;
             p = f > 0.0f;
             if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
@@ -601,6 +614,12 @@ __device__ __forceinline__ double solve_mode(double x0, double rd3, double kappa
 
 constexpr int kMaxBlock = 128;
 
+// the per-substep thermodynamics out of line, like the solver's other
+// once-per-cell or rare code, so that the FP64 growth loop stays compact
+__device__ __noinline__ Thermo thermo_cond(double th, double rv, double rd, double RH_max, double rdf) {
+    return thermo_eval_f<true>(th, rv, rd, RH_max, rdf);
+}
+
 template <int LPC, int MODE>
 __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
                            const double *rhod, Grid g, int sstp, double RH_max, int physics, DevStats *st) {
@@ -626,7 +645,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     const double rdf = rhod_factor(rd);
     for (int sub = 0; sub < sstp; ++sub) {
         {
-            const Thermo tt = thermo_eval_f<true>(thc, rvc, rd, RH_max, rdf);
+            const Thermo tt = thermo_cond(thc, rvc, rd, RH_max, rdf);
             if (sl == 0) {
                 s_t[gi] = tt;
                 s_tf[gi] = to_float(tt);
