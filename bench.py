@@ -444,12 +444,19 @@ def main():
                     frac=achieved / fp64_peak, traffic=COND_DRAM_BYTES_PER_LAUNCH,
                     flops_per_sd_substep=COND_FP64_FLOPS_PER_SD_SUBSTEP,
                     peak_source="derived: 4 FP64 flop/SM/clk x 152 SMs x sampled SM clock (1.25 TFLOP/s nominal)")
-    else:
+    elif tim["cond_launches"] > 0:
         bytes_per_launch = 40.0 * res["n_sd"]
         achieved = bytes_per_launch / (cond_ms * 1e-3) / 1e9
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = dict(kernel="k_condense", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
                     frac=achieved / hbm, traffic=None,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6800")
+    else:  # no condensation (the Golovin box): coalescence, 68 B per SD-step (read 36, write 32)
+        coal_ms = tim["coal_ms"] / max(1, tim["coal_launches"])
+        achieved = 68.0 * res["n_sd"] / (coal_ms * 1e-3) / 1e9
+        hbm = pk.get("hbm_gbs", 6800.0)
+        roof = dict(kernel="k_coal", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
+                    traffic=None, note="one cell of 8192 SDs: latency-bound, the state stays in L2",
                     peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6800")
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=res["t_dev"] / args.steps * 1e3, higher_is_better=True, scaling="weak",

@@ -4,19 +4,99 @@
 // the clone gets floor(N/2), the donor keeps the rest.
 //
 // Only run when the previous step left zeros (the host knows the count from
-// sdm_wait).  Zeros and donors are compacted, then both lists are sorted.
+// sdm_wait).  The nz zeros are compacted and sorted by id.  Of the donors
+// only the first nz in that order are needed: a radix select on N (eight
+// 8-bit digits, from the top) and then on the id among ties at the
+// threshold finds them without sorting every super-droplet, and only those
+// nz are compacted and sorted.
 #include "sdm_internal.cuh"
 
 namespace sdm {
 
-__global__ void k_rc_compact(SdArrays s, int64_t n, SortRec *zrec, SortRec *drec, DevStats *st) {
+constexpr int kSmemSort = 8192;  // records sorted in one block (128 KB)
+
+// zeros compacted; donors (N >= 2) counted
+__global__ void k_rc_compact(SdArrays s, int64_t n, SortRec *zrec, DevStats *st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool donor = false;
+    if (i < n) {
+        const unsigned long long N = s.N[i];
+        if (N == 0) {
+            const unsigned q = atomicAdd(&st->n_rc_zero, 1u);
+            zrec[q] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
+        }
+        donor = N >= 2;
+    }
+    const unsigned nd = __popc(__ballot_sync(0xffffffffu, donor));
+    if ((threadIdx.x & 31) == 0 && nd) atomicAdd(&st->n_rc_donor, nd);
+}
+
+// Radix select of the first k donors in (N descending, id ascending) order.
+struct RcSelect {
+    unsigned long long prefix, mask;  // the N digits fixed so far
+    unsigned k;                       // donors still to take at the current prefix
+    unsigned uprefix, umask;          // the id digits fixed so far (ties at N = prefix)
+};
+
+// digit histogram of the donors that match the fixed digits: of N (by_id =
+// 0) or, among N = prefix, of the id (by_id = 1)
+__global__ void k_rc_hist(SdArrays s, int64_t n, const RcSelect *sel, int shift, int by_id, unsigned *hist) {
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const RcSelect S = *sel;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long N = s.N[i];
+        if (N < 2) continue;
+        if (!by_id) {
+            if ((N & S.mask) == S.prefix) atomicAdd(&h[(unsigned)(N >> shift) & 255u], 1u);
+        } else if (N == S.prefix) {
+            const unsigned u = s.uid[i];
+            if ((u & S.umask) == S.uprefix) atomicAdd(&h[(u >> shift) & 255u], 1u);
+        }
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// fix the next digit: N from the largest bin down, ids from the smallest up
+__global__ void k_rc_pick(RcSelect *sel, unsigned *hist, int shift, int by_id) {
+    if (threadIdx.x != 0) return;
+    RcSelect S = *sel;
+    unsigned acc = 0;
+    for (int j = 0; j < 256; ++j) {
+        const int b = by_id ? j : 255 - j;
+        const unsigned c = hist[b];
+        if (acc + c >= S.k) {
+            S.k -= acc;
+            if (!by_id) {
+                S.prefix |= (unsigned long long)b << shift;
+                S.mask |= 255ull << shift;
+            } else {
+                S.uprefix |= (unsigned)b << shift;
+                S.umask |= 255u << shift;
+            }
+            break;
+        }
+        acc += c;
+    }
+    *sel = S;
+    for (int b = 0; b < 256; ++b) hist[b] = 0;
+}
+
+// the selected donors: N > T, or N = T with id <= U (take_all: every N >= 2)
+__global__ void k_rc_donors(SdArrays s, int64_t n, const RcSelect *sel, int take_all, SortRec *drec,
+                            DevStats *st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned long long N = s.N[i];
-    if (N == 0) {
-        const unsigned q = atomicAdd(&st->n_rc_zero, 1u);
-        zrec[q] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
-    } else if (N >= 2) {
+    if (N < 2) return;
+    bool take = take_all;
+    if (!take) {
+        const RcSelect S = *sel;
+        take = N > S.prefix || (N == S.prefix && s.uid[i] <= S.uprefix);
+    }
+    if (take) {
         const unsigned q = atomicAdd(&st->n_rc_donor, 1u);
         drec[q] = SortRec{~N, s.uid[i], (uint32_t)i};  // ascending ~N = descending N
     }
@@ -41,10 +121,8 @@ cudaError_t launch_recycle_compact(sdm_ctx *c) {
     cudaError_t e = cudaMemsetAsync(&c->dstats->n_rc_zero, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     SortRec *zrec = (SortRec *)c->rc_tmp;
-    SortRec *drec = zrec + (c->rc_tmp_bytes / sizeof(SortRec)) / 2;
     const int B = 256;
-    k_rc_compact<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->buf[c->cur], c->n_sd, zrec, drec,
-                                                            c->dstats);
+    k_rc_compact<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->buf[c->cur], c->n_sd, zrec, c->dstats);
     return cudaGetLastError();
 }
 
@@ -54,19 +132,44 @@ static uint32_t pow2_at_least(uint32_t n) {
     return p;
 }
 
+// nz zeros and nd donors counted by launch_recycle_compact
 cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd) {
     SortRec *zrec = (SortRec *)c->rc_tmp;
     SortRec *drec = zrec + (c->rc_tmp_bytes / sizeof(SortRec)) / 2;
-    cudaError_t e = sort_records(zrec, nz, pow2_at_least(nz), c->stream);
-    if (e == cudaSuccess) e = sort_records(drec, nd, pow2_at_least(nd), c->stream);
-    if (e != cudaSuccess) return e;
+    RcSelect *sel = (RcSelect *)(c->rc_sel);
+    unsigned *hist = (unsigned *)(sel + 1);
     const uint32_t np = nz < nd ? nz : nd;
     const int B = 256;
+    // every donor is taken, or they all fit one block's shared-memory sort:
+    // sort them all and use the first np
+    const int take_all = nd <= nz || nd <= (uint32_t)kSmemSort;
+    const uint32_t ns = take_all ? nd : np;  // donor records compacted and sorted
+    const int hist_blocks = 4 * 152;
+    int launches = 0;
+    if (!take_all) {
+        RcSelect init{0ull, 0ull, np, 0u, 0u};
+        cudaError_t e = cudaMemcpyAsync(sel, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) return e;
+        for (int by_id = 0; by_id < 2; ++by_id) {
+            for (int shift = by_id ? 24 : 56; shift >= 0; shift -= 8) {
+                k_rc_hist<<<hist_blocks, 256, 0, c->stream>>>(c->buf[c->cur], c->n_sd, sel, shift, by_id, hist);
+                k_rc_pick<<<1, 32, 0, c->stream>>>(sel, hist, shift, by_id);
+                launches += 2;
+            }
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(&c->dstats->n_rc_donor, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return e;
+    k_rc_donors<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->buf[c->cur], c->n_sd, sel, take_all, drec, c->dstats);
+    e = sort_records(zrec, nz, pow2_at_least(nz), c->stream);
+    if (e == cudaSuccess) e = sort_records(drec, ns, pow2_at_least(ns), c->stream);
+    if (e != cudaSuccess) return e;
     k_rc_apply<<<grid_for(np, B), B, 0, c->stream>>>(c->buf[c->cur], zrec, drec, np);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     c->host_recycled += np;
-    c->tacc.launches += 1 + (nz > 1 ? 2 : 0) + (nd > 1 ? 2 : 0);  // apply, fills and sorts
+    c->tacc.launches += launches + 2 + (nz > 1 ? 2 : 0) + (ns > 1 ? 2 : 0);  // select, donors, apply, sorts
     return cudaSuccess;
 }
 
@@ -79,8 +182,6 @@ __global__ void k_fill_max(SortRec *r, uint32_t from, uint32_t to) {
     const uint32_t i = from + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < to) r[i] = SortRec{~0ull, ~0u, ~0u};
 }
-
-constexpr int kSmemSort = 8192;  // records sorted in one block (128 KB)
 
 __global__ void __launch_bounds__(1024) k_sort_smem(SortRec *r, uint32_t npow2) {
     extern __shared__ SortRec s[];

@@ -215,6 +215,7 @@ void free_ctx(sdm_ctx *c) {
     for (int d = 0; d < 3; ++d) cudaFree(c->rhoC[d]);
     cudaFree(c->scan_tmp);
     cudaFree(c->rc_tmp);
+    cudaFree(c->rc_sel);
     cudaFree(c->dstats);
     if (c->hstats) cudaFreeHost(c->hstats);
     for (auto &t : c->timers) {
@@ -431,6 +432,7 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
     if (e == cudaSuccess) e = dalloc(&c->scan_tmp, nc / 1024 + 2);
     c->rc_tmp_bytes = 2 * npow2 * sizeof(SortRec);
     if (e == cudaSuccess) e = cudaMalloc(&c->rc_tmp, c->rc_tmp_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->rc_sel, 4096);
     if (e == cudaSuccess) e = dalloc(&c->dstats, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hstats, sizeof(DevStats));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done_event, cudaEventDisableTiming);

@@ -273,6 +273,7 @@ struct sdm_ctx {
     uint32_t *scan_tmp = nullptr;
     void *rc_tmp = nullptr;
     size_t rc_tmp_bytes = 0;
+    void *rc_sel = nullptr;  // recycling's radix-select state and histogram (4 KB)
     sdm::DevStats *dstats = nullptr;
     sdm::DevStats *hstats = nullptr;  // pinned landing area of stats copies
     sdm::DevStats mirror{};           // last copy pulled from the device

@@ -180,13 +180,17 @@ def test_full_steps_3d_small():
     compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
 
 
-def test_recycling_matches_oracle():
+@pytest.mark.parametrize("zero_fraction", [0.2, 0.8])
+def test_recycling_matches_oracle(zero_fraction):
+    """Zeros take donors in (N descending, id ascending) order.  With a fifth
+    of the multiplicities zeroed the donors are selected (radix select on N,
+    then on the id among ties); with four fifths every donor is taken."""
     w = small_2d(9)
     p, o = pair(w)
-    # zero out a pseudo-random fifth of the multiplicities on both sides
+    # zero out a pseudo-random share of the multiplicities on both sides
     g = p.state()
     rng = np.random.default_rng(0)
-    zero_ids = set(rng.choice(len(g["uid"]), size=len(g["uid"]) // 5, replace=False).tolist())
+    zero_ids = set(rng.choice(len(g["uid"]), size=int(len(g["uid"]) * zero_fraction), replace=False).tolist())
     uid_store = p.attr("uid")
     N_store = p.attr("N")
     N_store[[i for i, u in enumerate(uid_store) if int(u) in zero_ids]] = 0
@@ -201,6 +205,29 @@ def test_recycling_matches_oracle():
     o.step_async(opts)
     compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
     assert p.stats()["n_recycled"] == o.stats.n_recycled > 0
+
+
+def test_recycling_select_with_ties():
+    """More donors than one block sorts (18 000 super-droplets), a fifth of
+    them zeroed, and the multiplicities forced onto three values, so that the
+    donors at the threshold are picked by id: the radix select on N and then
+    on the id must reproduce the oracle's (N descending, id ascending) order."""
+    w = small_2d(12, nx=30, nz=30, sd=20)
+    p, o = pair(w)
+    uid_store = p.attr("uid").astype(np.int64)
+    N_by_uid = 1000 + (np.arange(len(uid_store)) * 7919) % 3  # 1000, 1001, 1002
+    rng = np.random.default_rng(3)
+    zero = rng.choice(len(uid_store), size=len(uid_store) // 5, replace=False)
+    N_by_uid[zero] = 0
+    sdm.sdm_set_attr(p.ctx, "N", N_by_uid[uid_store].astype(np.uint64))
+    o.state.N[:] = N_by_uid[o.state.uid.astype(np.int64)]
+    opts = dict(COAL_ONLY, coal=0)
+    for _ in range(2):
+        p.step_async(opts)
+        p.wait()  # the first wait learns about the zeros
+        o.step_async(opts)
+    compare_states(p.state(), oracle_state(o, present_dims(w.cfg)))
+    assert p.stats()["n_recycled"] == o.stats.n_recycled == len(zero)
 
 
 def test_diagnostics_match_oracle():
