@@ -315,13 +315,21 @@ def dist_barrier(world):
 
 
 def dist_max(v, world):
+    """The maximum of v over the ranks (the slowest rank's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(n_sd_per_rank: int, steps: int, world: int, t_max: float) -> float:
+    """SD-steps/s of the whole job: every rank runs its own replica of the
+    workload (seeded by its rank) for the same steps, and the job takes as
+    long as its slowest rank."""
+    return n_sd_per_rank * steps * world / t_max
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -425,7 +433,7 @@ def main():
         return
     w = res["w"]
     total_sd_steps = res["n_sd"] * args.steps * world
-    value = total_sd_steps / res["t_dev"]
+    value = whole_job_value(res["n_sd"], args.steps, world, res["t_dev"])
     tim = res["timing"]
     pk = peaks()
     # dominant kernel: condensation, bound by FP64 arithmetic.  Its FP64 work
