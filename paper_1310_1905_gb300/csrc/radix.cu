@@ -39,27 +39,65 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K *key, int64_t n,
     hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];  // digit-major
 }
 
-// K: the type of the word being sorted on; P: a passenger word moved along
+// The stable scatter of one pass (K: the word sorted on; P: a passenger
+// word moved along), with the tile staged in shared memory: every tile
+// ranks its records by digit in their original order (warp match_any), puts
+// them there in digit order, and then every digit's run leaves as
+// consecutive writes (a direct scatter writes each record to its own bin,
+// about one 32-byte transaction per record).  offs is the
+// exclusive scan of the digit-major tile histogram, so a tile's count of
+// digit d is the step to the next entry.
 template <class K, class P>
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *key_in, const uint32_t *val_in,
-                                                           const P *aux_in, K *key_out,
-                                                           uint32_t *val_out, P *aux_out,
-                                                           int64_t n, int shift, const uint32_t *offs,
-                                                           int n_tiles) {
-    __shared__ uint32_t base_d[256];      // running position of each digit
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter_staged(const K *key_in, const uint32_t *val_in,
+                                                                  const P *aux_in, K *key_out,
+                                                                  uint32_t *val_out, P *aux_out, int64_t n,
+                                                                  int shift, const uint32_t *offs,
+                                                                  int n_tiles) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    K *skey = reinterpret_cast<K *>(sm);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kRsTile);
+    P *saux = reinterpret_cast<P *>(sval + kRsTile);
+    __shared__ uint32_t start[256], gbase[256], run[256];
     __shared__ uint32_t wcnt[kRsWarps][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    base_d[threadIdx.x] = offs[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d0 = threadIdx.x;
     const int64_t tile0 = (int64_t)blockIdx.x * kRsTile;
+    const int cnt_tile = n - tile0 < kRsTile ? (int)(n - tile0) : kRsTile;
+    {
+        const int64_t idx = (int64_t)d0 * n_tiles + blockIdx.x;
+        const uint32_t o = offs[idx];
+        const uint32_t next = idx + 1 < (int64_t)256 * n_tiles ? offs[idx + 1] : (uint32_t)n;
+        gbase[d0] = o;
+        start[d0] = next - o;  // the tile's count of this digit, scanned below
+        run[d0] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 counts by one warp
+        uint32_t v[8], tot = 0;
+        for (int j = 0; j < 8; ++j) {
+            v[j] = start[lane * 8 + j];
+            tot += v[j];
+        }
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        uint32_t acc = incl - tot;
+        for (int j = 0; j < 8; ++j) {
+            start[lane * 8 + j] = acc;
+            acc += v[j];
+        }
+    }
+    __syncthreads();
     for (int i = 0; i < kRsItems; ++i) {
         for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
         __syncthreads();
-        const int64_t q = tile0 + (int64_t)i * kRsThreads + threadIdx.x;
-        const bool ok = q < n;
+        const int j = i * kRsThreads + threadIdx.x;
+        const bool ok = j < cnt_tile;
         K k = 0;
         uint32_t dg = 0xffffffffu;
         if (ok) {
-            k = key_in[q];
+            k = key_in[tile0 + j];
             dg = digit_of(k, shift);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
@@ -67,19 +105,42 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *key_in, cons
         if (ok && lower == 0) wcnt[w][dg] = __popc(peers);
         __syncthreads();
         if (ok) {
-            uint32_t pos = base_d[dg] + __popc(lower);
+            uint32_t pos = start[dg] + run[dg] + __popc(lower);
             for (int v = 0; v < w; ++v) pos += wcnt[v][dg];
-            key_out[pos] = k;
-            val_out[pos] = val_in[q];
-            if (aux_in) aux_out[pos] = aux_in[q];
+            skey[pos] = k;
+            sval[pos] = val_in[tile0 + j];
+            if (aux_in) saux[pos] = aux_in[tile0 + j];
         }
         __syncthreads();
-        // advance the running bases by this round's counts
         uint32_t add = 0;
         for (int v = 0; v < kRsWarps; ++v) add += wcnt[v][threadIdx.x];
-        base_d[threadIdx.x] += add;
+        run[threadIdx.x] += add;
         __syncthreads();
     }
+    for (int j = threadIdx.x; j < cnt_tile; j += kRsThreads) {
+        const K k = skey[j];
+        const uint32_t d = digit_of(k, shift);
+        const uint32_t pos = gbase[d] + (uint32_t)j - start[d];
+        key_out[pos] = k;
+        val_out[pos] = sval[j];
+        if (aux_in) aux_out[pos] = saux[j];
+    }
+}
+
+template <class K, class P>
+static size_t staged_smem() {
+    return (size_t)kRsTile * (sizeof(K) + sizeof(uint32_t) + sizeof(P));
+}
+
+template <class K, class P>
+static cudaError_t staged_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_rs_scatter_staged<K, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)staged_smem<K, P>());
+    done = e == cudaSuccess;
+    return e;
 }
 
 // Sort n records by (aux, key) where aux < 2^(8*aux_bytes) and only the
@@ -102,13 +163,19 @@ cudaError_t radix_sort_pairs(K *key_a, uint32_t *val_a, uint32_t *aux_a, K *key_
             k_rs_hist<K><<<tiles, kRsThreads, 0, st>>>(ka, n, shift, hist, tiles);
             cudaError_t e = scan_counts(hist, hist, scan_tmp, 256 * tiles, st);
             if (e != cudaSuccess) return e;
-            k_rs_scatter<K, uint32_t><<<tiles, kRsThreads, 0, st>>>(ka, va, xa, kb, vb, xb, n, shift, hist, tiles);
+            e = staged_attr<K, uint32_t>();
+            if (e != cudaSuccess) return e;
+            k_rs_scatter_staged<K, uint32_t><<<tiles, kRsThreads, staged_smem<K, uint32_t>(), st>>>(
+                ka, va, xa, kb, vb, xb, n, shift, hist, tiles);
         } else {
             // sort by aux: aux acts as the key, the key rides along
             k_rs_hist<uint32_t><<<tiles, kRsThreads, 0, st>>>(xa, n, shift, hist, tiles);
             cudaError_t e = scan_counts(hist, hist, scan_tmp, 256 * tiles, st);
             if (e != cudaSuccess) return e;
-            k_rs_scatter<uint32_t, K><<<tiles, kRsThreads, 0, st>>>(xa, va, ka, xb, vb, kb, n, shift, hist, tiles);
+            e = staged_attr<uint32_t, K>();
+            if (e != cudaSuccess) return e;
+            k_rs_scatter_staged<uint32_t, K><<<tiles, kRsThreads, staged_smem<uint32_t, K>(), st>>>(
+                xa, va, ka, xb, vb, kb, n, shift, hist, tiles);
         }
         std::swap(ka, kb);
         std::swap(va, vb);
