@@ -139,7 +139,9 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
     const float eps = 5.9604645e-8f;  // 2^-24
     *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 4.0f * Ar)) + 64.0f * fabsf(g));
     if (DG != kDgNone) {
-        const float drho_dr = t.rho_vs * kel * (3.0f * r * r * rd3 * kappa / (den * den) - aw * t.A / (r * r));
+        // 3 r^2 rd3 kappa / den^2 without squaring den (~1e-24 m^3 for 10 nm
+        // droplets, whose square underflows FP32)
+        const float drho_dr = t.rho_vs * kel * (3.0f * kappa * fdiv(rd3, den) * fdiv(x, den) - aw * fdiv(t.A, x));
         // D_eff = 1 / (1/D + Dterm/K): d ln D_eff = (D_eff/D) d ln D + (1 - D_eff/D) d ln K
         const float wD = Deff / D;
         const float dlnc = wD * dlnD + (1.0f - wD) * dlnK;
@@ -247,9 +249,10 @@ SDM_HD __noinline__ double fres_rare(double x, double x0, double rd3, double kap
 struct FastSolve {
     double x0, rd3, kappa;
     double a, b, lo, hi, xk, xp, fp, slope, sdx, sdf, x1;
+    double rd2;  // r_d^2 when the bracket's lower end is clamped to it
     float Lu, Hu, mu;
     int k;
-    bool plo, undecided, mu_inside, pmu, have_slope;
+    bool plo, undecided, mu_inside, pmu, have_slope, clamp;
 };
 
 // The growth rate for the fast solve, one evaluation for both of its uses
@@ -301,66 +304,27 @@ SDM_HD __noinline__ double bisect_rest(double lo, double hi, bool plo, double x0
 
 // After g0 = g(x0): bracket, ends, Euler step, locate.  Returns true when
 // the solve is finished (S.x1 set); otherwise S.xk is the first polish point.
-SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
-                        SolveCounters &cnt) {
+// 1. locate: from the bracket [x0 + L, x0 + H] (FP32 increments) whose ends
+//    have the signs plo and !plo, halve in FP32 while FP32 decides - the
+//    halves the FP64 bisection takes, up to FP32 rounding of the midpoints -
+//    and set up the polish at the point mu where it stops deciding.
+SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &tf, double dtp, int physics) {
     const double x0 = S.x0;
-    const double a = fmax(rd2_of(S.rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
-    const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
-    S.a = a;
-    S.b = b;
     const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
-    // 1. ends and locate.  The sign of f at x0 + d (d an FP32 increment) is
-    //    computed in FP32 and trusted where |f| exceeds its error bound (it
-    //    is then the sign an FP64 evaluation gives).  Points k = 0, 1 are the
-    //    bracket's ends (at x0 itself f = -dtp g0 exactly); from k = 2 the
-    //    increment's bracket is halved while FP32 decides - the halves the
-    //    FP64 bisection takes, up to FP32 rounding of the midpoints.
-    float L = (float)(a - x0), H = (float)(b - x0), mu = 0.0f, dg_last = 0.0f;
-    bool pa = false, plo = false, undecided = false;
-    for (int k = 0; k < 66; ++k) {
-        float d;
-        if (k < 2) {
-            d = k ? H : L;
-        } else {
-            d = 0.5f * (L + H);
-            if (!(d > L && d < H)) break;
+    float mu = 0.0f;
+    bool undecided = false;
+    for (int k = 0; k < 64; ++k) {
+        const float d = 0.5f * (L + H);
+        if (!(d > L && d < H)) break;
+        const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
+        const float f = d - dtpf * q.g;
+        if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
+            mu = d;
+            undecided = true;
+            break;
         }
-        bool p;
-        const double xe = k ? b : a;
-        if (k < 2 && xe == x0) {
-            p = -dtp * g0 > 0.0;
-        } else {
-            const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
-            const float f = d - dtpf * q.g;
-            p = f > 0.0f;
-            if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
-                if (k < 2) {
-                    p = fres_rare(xe, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
-                } else {
-                    mu = d;
-                    undecided = true;
-                    break;
-                }
-            }
-        }
-        if (k == 0) {
-            pa = p;
-        } else if (k == 1) {
-            if (pa == p) {  // f keeps its strict sign: the Euler step
-                cnt.euler++;
-                S.x1 = 0.5 * (a + b);
-                return true;
-            }
-            plo = pa;
-            if (b - a <= 0x1p-52 * b) {  // the bisection's own first exit
-                S.x1 = 0.5 * (a + b);
-                return true;
-            }
-        } else if (p == plo) {
-            L = d;
-        } else {
-            H = d;
-        }
+        if ((f > 0.0f) == plo) L = d;
+        else H = d;
     }
     S.plo = plo;
     S.undecided = undecided;
@@ -369,11 +333,11 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     if (!undecided) mu = 0.5f * (L + H);
     S.mu = mu;
     // f' at mu for the first Newton step (D_eff's variation included)
-    dg_last = growth_f3_full(x0f + mu, rd3f, kf, &tf, physics).dg;
+    const float dg = growth_f3_full(x0f + mu, rd3f, kf, &tf, physics).dg;
     // 2. the polish starts at mu inside [lo, hi]
     double lo = x0 + (double)L, hi = x0 + (double)H;
-    if (!(lo >= a)) lo = a;
-    if (!(hi <= b)) hi = b;
+    if (!(lo >= S.a)) lo = S.a;
+    if (!(hi <= S.b)) hi = S.b;
     double xk = x0 + (double)mu;
     S.mu_inside = xk > lo && xk < hi;
     if (!S.mu_inside) xk = 0.5 * (lo + hi);
@@ -381,12 +345,158 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     S.hi = hi;
     S.xk = xk;
     S.xp = S.fp = 0.0;
-    S.slope = 1.0 - dtp * (double)dg_last;  // Newton with the FP32 derivative first
+    S.slope = 1.0 - dtp * (double)dg;  // Newton with the FP32 derivative first
     S.sdx = S.sdf = 1.0;
     S.have_slope = true;
     S.pmu = false;
     S.k = 0;
+}
+
+// After g0 = g(x0) in FP64: the paper's bracket and Euler test exactly, then
+// the locate.  Returns true when the solve is finished (S.x1 set).
+SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                        SolveCounters &cnt) {
+    const double x0 = S.x0;
+    const double a = fmax(rd2_of(S.rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
+    const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
+    S.a = a;
+    S.b = b;
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
+    // the ends' signs; at x0 itself f = -dtp g0 exactly.  The sign of f at
+    // x0 + d (d an FP32 increment) is computed in FP32 and trusted where |f|
+    // exceeds its error bound (it is then the sign an FP64 evaluation gives).
+    bool pe[2];
+    for (int e = 0; e < 2; ++e) {
+        const double xe = e ? b : a;
+        if (xe == x0) {
+            pe[e] = -dtp * g0 > 0.0;
+        } else {
+            const float d = (float)(xe - x0);
+            const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
+            const float f = d - dtpf * q.g;
+            pe[e] = fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err
+                        ? f > 0.0f
+                        : fres_rare(xe, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
+        }
+    }
+    if (pe[0] == pe[1]) {  // f keeps its strict sign: the Euler step
+        cnt.euler++;
+        S.x1 = 0.5 * (a + b);
+        return true;
+    }
+    if (b - a <= 0x1p-52 * b) {  // the bisection's own first exit
+        S.x1 = 0.5 * (a + b);
+        return true;
+    }
+    // x0 is an end of the bracket and f(x0) = -dt' g0 is known: the polish
+    // starts at the Newton step from it (with the FP32 f').  These are the
+    // solves whose g0 FP32 could not sign, close to equilibrium, where the
+    // bracket is narrow and the step lands near the root; the replay starts
+    // from the whole bracket.  x0 is not a secant point: g0 was formed as
+    // growth() forms it, the polish residuals in the one-division form, and
+    // over a step of a few ulps their difference is rounding.
+    S.plo = pe[0];
+    S.undecided = true;
+    S.Lu = (float)(a - x0);
+    S.Hu = (float)(b - x0);
+    S.mu = 0.0f;
+    S.mu_inside = false;
+    S.pmu = false;
+    S.lo = a;
+    S.hi = b;
+    const float dg = growth_f3_full(x0f, rd3f, kf, &tf, physics).dg;
+    S.slope = 1.0 - dtp * (double)dg;
+    S.have_slope = true;
+    S.sdx = S.sdf = 1.0;
+    const double f0 = -dtp * g0;
+    double xk = S.slope > 0.0 ? x0 - f0 / S.slope : 0.5 * (a + b);
+    if (!(xk > a && xk < b)) xk = 0.5 * (a + b);
+    S.xp = S.fp = 0.0;
+    S.xk = xk;
+    S.k = 0;
     return false;
+}
+
+// How a solve starts, decided from g(x0) in FP32:
+enum { kStartPolish = 0, kStartEuler = 1, kStartTiny = 2, kStartExact = 3 };
+// kStartPolish: f changes sign over the bracket; the locate is done and the
+//   first FP64 evaluation is the polish's.
+// kStartEuler, kStartTiny: the Euler step, or a bracket below FP64
+//   resolution; x1 = (a + b)/2 needs g(x0) in FP64.
+// kStartExact: FP32 cannot decide; the paper's path from g(x0) in FP64.
+//
+// With g0 known to +-e0, the moving end of the bracket x0 + 2 dt' g0 is
+// known to +-u; the sign of f there is trusted only where |f| exceeds the
+// FP32 bound plus |f'| u, so every decision taken here is the one the FP64
+// bracket gives.  Only the Euler step, whose result is g(x0) itself, then
+// needs g(x0) in FP64: the other solves save that evaluation.
+SDM_HD int fs_start(FastSolve &S, const ThermoF &tf, double dtp, int physics) {
+    const double x0 = S.x0;
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
+    const GF q0 = growth_f3_call(x0f, rd3f, kf, &tf, physics);
+    if (!(fabsf(q0.g) > q0.err)) return kStartExact;  // the sign of g0
+    const bool grow = q0.g > 0.0f;
+    const float dE = 2.0f * dtpf * q0.g;                          // the moving end's increment
+    const float u = 2.0f * dtpf * q0.err + 2.4e-7f * fabsf(dE);   // and its uncertainty
+    float rd2f = cbrtf(rd3f);
+    rd2f *= rd2f;
+    const float rtol = 1e-6f * rd2f;
+    // the sign of f at x0 + d, d known to +-ud; ok = decided
+    auto sign_at = [&](float d, float ud, bool *ok) -> bool {
+        const GF q = growth_f3<kDgKoehler>(x0f + d, rd3f, kf, tf, physics);
+        const float f = d - dtpf * q.g;
+        const float fpr = 1.0f + 2.0f * dtpf * (fabsf(q.dg) + fabsf(q.g) / (x0f + d));  // >= |f'|
+        *ok = fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err + fpr * ud;
+        return f > 0.0f;
+    };
+    bool ok, pa, pb;
+    float L, H;
+    S.clamp = false;
+    if (grow) {  // a = max(r_d^2, x0) = x0 with f(x0) = -dt' g0 < 0; b = x0 + dE
+        if (!(x0f > rd2f + rtol)) return kStartExact;
+        pa = false;
+        pb = sign_at(dE, u, &ok);
+        if (!ok) return kStartExact;
+        L = 0.0f;
+        H = dE;
+        S.a = x0;
+        S.b = x0 + (double)dE;
+    } else {  // b = x0 with f(x0) > 0; a = max(r_d^2, x0 + dE)
+        pb = true;
+        const double xa = x0 + (double)dE;
+        if (xa > (double)(rd2f + rtol) + (double)u) {
+            pa = sign_at(dE, u, &ok);
+            L = dE;
+            S.a = xa;
+        } else if (xa < (double)(rd2f - rtol) - (double)u) {
+            S.clamp = true;
+            S.rd2 = rd2_of(S.rd3);
+            L = (float)(S.rd2 - x0);
+            pa = sign_at(L, 0.0f, &ok);
+            S.a = S.rd2;
+        } else {
+            return kStartExact;
+        }
+        if (!ok) return kStartExact;
+        H = 0.0f;
+        S.b = x0;
+    }
+    if (pa == pb) return kStartEuler;
+    // the bisection's own first exit, b - a <= 2^-52 b
+    const double w = (double)(H - L), uw = S.clamp ? 0.0 : (double)u;
+    if (w + uw <= 0x1p-52 * (S.b - uw)) return kStartTiny;
+    if (!(w - uw > 0x1p-52 * (S.b + uw))) return kStartExact;
+    fs_locate(S, L, H, pa, tf, dtp, physics);
+    return kStartPolish;
+}
+
+// x1 of the Euler step (or of a bracket below resolution) from g0 in FP64:
+// the paper's (a + b)/2, with the clamp of a that fs_start decided
+SDM_HD double fs_euler(const FastSolve &S, double g0, double dtp) {
+    const double x0 = S.x0;
+    const double a = S.clamp ? S.rd2 : x0 + fmin(2.0 * dtp * g0, 0.0);
+    const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
+    return 0.5 * (a + b);
 }
 
 // 3. replay: near activation f need not be monotonic, and a bracket can hold
@@ -513,13 +623,23 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     S.x0 = x0;
     S.rd3 = rd3;
     S.kappa = kappa;
-    // g(x0), then one growth evaluation per polish step, through one call site
-    for (int k = 0; k < 14; ++k) {
-        const bool first = k == 0;
+    // The first FP64 evaluation is g(x0) where the start needs it (an Euler
+    // step, or FP32 could not decide), else the polish's first; then one per
+    // polish step, all through one call site.
+    const int start = fs_start(S, tf, dtp, physics);
+    for (int k = 0; k < 15; ++k) {
+        const bool g0 = k == 0 && start != kStartPolish;
         double mag;
-        const double v = growth_eval(first ? x0 : S.xk, first, rd3, kappa, t, physics, &mag);
-        if (first ? fs_after_g0(S, v, t, tf, dtp, physics, cnt) : fs_after_polish(S, v, mag, t, tf, dtp, physics, cnt))
-            return S.x1;
+        const double v = growth_eval(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
+        if (g0) {
+            if (start == kStartExact) {
+                if (fs_after_g0(S, v, t, tf, dtp, physics, cnt)) return S.x1;
+                continue;
+            }
+            if (start == kStartEuler) cnt.euler++;
+            return fs_euler(S, v, dtp);
+        }
+        if (fs_after_polish(S, v, mag, t, tf, dtp, physics, cnt)) return S.x1;
     }
     return S.x1;  // not reached: the polish finishes within 13 evaluations
 }
