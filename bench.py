@@ -43,8 +43,8 @@ N_SM = 152
 # ncu, k_condense on the 2D case (profiles/k_condense_icmw_2d_fp64.md):
 # FP64 flops the kernel executes (2 DFMA + DADD + DMUL) per SD-substep, and
 # DRAM bytes read + written per launch
-COND_FP64_FLOPS_PER_SD_SUBSTEP = 836.1
-COND_DRAM_BYTES_PER_LAUNCH = 12.12e6
+COND_FP64_FLOPS_PER_SD_SUBSTEP = 649.8
+COND_DRAM_BYTES_PER_LAUNCH = 11.81e6
 
 
 def parse():
