@@ -91,15 +91,15 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double 
     atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// collection kernel: geometric (E = 1) or Golovin
-__device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, double rw2b,
-                                           double vta, double vtb) {
+// collection kernel: geometric (E = 1) or Golovin; ra = sqrt(rw2a), rb =
+// sqrt(rw2b), kept per super-droplet by the callers
+__device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, double ra, double rw2b,
+                                           double rb, double vta, double vtb) {
     if (p.kernel == SDM_KERNEL_GOLOVIN) {
-        const double Va = 4.0 / 3.0 * phys::pi * rw2a * sqrt(rw2a);
-        const double Vb = 4.0 / 3.0 * phys::pi * rw2b * sqrt(rw2b);
+        const double Va = 4.0 / 3.0 * phys::pi * rw2a * ra;
+        const double Vb = 4.0 / 3.0 * phys::pi * rw2b * rb;
         return p.golovin_b * (Va + Vb);
     }
-    const double ra = sqrt(rw2a), rb = sqrt(rw2b);
     const double dv = fabs(vta - vtb);
     return phys::pi * (ra + rb) * (ra + rb) * dv;
 }
@@ -107,12 +107,12 @@ __device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, dou
 // Mixed-precision mode: terminal velocities, the kernel and P in FP32, a
 // 24-bit uniform number and 32-bit shuffle keys (ties still broken by id);
 // merged radii stay FP64 so that r^3 is conserved to FP64 rounding.
-__device__ __forceinline__ double vt_of(const CoalParams &p, double rw2, double nu, double cX) {
-    return p.mixed ? (double)vterm_f((float)rw2, (float)nu, (float)cX) : vterm(rw2, nu, cX);
+__device__ __forceinline__ double vt_of(const CoalParams &p, double rw2, double r, double nu, double cX) {
+    return p.mixed ? (double)vterm_f((float)rw2, (float)nu, (float)cX) : vterm_r(rw2, r, nu, cX);
 }
 
-__device__ __forceinline__ double prob(const CoalParams &p, unsigned long long Nmax, double rwa,
-                                       double rwb, double va, double vb, double dtpp, double scale) {
+__device__ __forceinline__ double prob(const CoalParams &p, unsigned long long Nmax, double rwa, double ra,
+                                       double rwb, double rb, double va, double vb, double dtpp, double scale) {
     if (p.mixed) {
         float K;
         if (p.kernel == SDM_KERNEL_GOLOVIN) {
@@ -124,7 +124,7 @@ __device__ __forceinline__ double prob(const CoalParams &p, unsigned long long N
         }
         return (double)((float)Nmax * K * (float)dtpp / (float)p.g.dV * (float)scale);
     }
-    const double K = kernel_K(p, rwa, rwb, va, vb);
+    const double K = kernel_K(p, rwa, ra, rwb, rb, va, vb);
     return (double)Nmax * K * dtpp / p.g.dV * scale;
 }
 
@@ -146,8 +146,7 @@ __device__ __forceinline__ int collide(Acc &A, int a, int b) {
     const int L = A.N(a) >= A.N(b) ? a : b;
     const int S = L == a ? b : a;
     A.setN(L, A.N(L) - A.N(S));
-    const double rwS = A.rw2(S), rwL = A.rw2(L);
-    const double r3 = rwS * sqrt(rwS) + rwL * sqrt(rwL);
+    const double r3 = A.rw2(S) * A.r(S) + A.rw2(L) * A.r(L);
     const double r = cbrt(r3);
     A.setrw2(S, r * r);
     const double dS = A.rd3(S), dL = A.rd3(L);
@@ -161,7 +160,7 @@ __device__ __forceinline__ int collide(Acc &A, int a, int b) {
 template <int CAP>
 struct WarpSmem {
     unsigned long long N[CAP], acc[CAP];
-    double rw2[CAP], rd3[CAP], kappa[CAP], vt[CAP];
+    double rw2[CAP], r[CAP], rd3[CAP], kappa[CAP], vt[CAP];
     uint32_t uid[CAP];
 };
 
@@ -170,10 +169,14 @@ struct SmemAcc {
     WarpSmem<CAP> *w;
     __device__ unsigned long long N(int i) const { return w->N[i]; }
     __device__ double rw2(int i) const { return w->rw2[i]; }
+    __device__ double r(int i) const { return w->r[i]; }
     __device__ double rd3(int i) const { return w->rd3[i]; }
     __device__ double kappa(int i) const { return w->kappa[i]; }
     __device__ void setN(int i, unsigned long long v) { w->N[i] = v; }
-    __device__ void setrw2(int i, double v) { w->rw2[i] = v; }
+    __device__ void setrw2(int i, double v) {
+        w->rw2[i] = v;
+        w->r[i] = sqrt(v);
+    }
     __device__ void setrd3(int i, double v) { w->rd3[i] = v; }
     __device__ void setkappa(int i, double v) { w->kappa[i] = v; }
 };
@@ -216,11 +219,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             const uint32_t pi = (uint32_t)(v[r].pk & 0xffffffffu);
             const uint32_t id = (uint32_t)(v[r].pk >> 32);
             W.N[q] = src.N[pi];
-            W.rw2[q] = src.rw2[pi];
+            const double rw2 = src.rw2[pi];
+            W.rw2[q] = rw2;
+            W.r[q] = sqrt(rw2);
             W.rd3[q] = src.rd3[pi];
             W.kappa[q] = src.kappa[pi];
             W.uid[q] = id;
-            W.vt[q] = geo ? vt_of(p, W.rw2[q], nu, cX) : 0.0;
+            W.vt[q] = geo ? vt_of(p, rw2, W.r[q], nu, cX) : 0.0;
             if (p.g.nx > 0) dst.x[beg + q] = src.x[pi];
             if (p.g.ny > 0) dst.y[beg + q] = src.y[pi];
             if (p.g.nz > 0) dst.z[beg + q] = src.z[pi];
@@ -271,13 +276,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 if (mine && pos + 1 < m) {
                     const int a = (int)(ka.pk & 0xffu), b = (int)(kb.pk & 0xffu);
                     const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
-                    const double P = prob(p, Nmax, W.rw2[a], W.rw2[b], W.vt[a], W.vt[b], dtpp, scale);
+                    const double P = prob(p, Nmax, W.rw2[a], W.r[a], W.rw2[b], W.r[b], W.vt[a], W.vt[b], dtpp,
+                                          scale);
                     n_pairs++;
                     if (P > 1.0) n_pgt1++;
                     max_p = fmax(max_p, P);
                     if (accepted(p, W.acc[a], P)) {
                         const int S = collide(A, a, b);
-                        if (geo) W.vt[S] = vt_of(p, W.rw2[S], nu, cX);
+                        if (geo) W.vt[S] = vt_of(p, W.rw2[S], W.r[S], nu, cX);
                         n_coll++;
                     }
                 }
@@ -318,6 +324,7 @@ struct GlobalAcc {
     uint32_t beg;
     __device__ unsigned long long N(int i) const { return s.N[beg + i]; }
     __device__ double rw2(int i) const { return s.rw2[beg + i]; }
+    __device__ double r(int i) const { return sqrt(s.rw2[beg + i]); }
     __device__ double rd3(int i) const { return s.rd3[beg + i]; }
     __device__ double kappa(int i) const { return s.kappa[beg + i]; }
     __device__ void setN(int i, unsigned long long v) { s.N[beg + i] = v; }
@@ -430,11 +437,11 @@ __global__ void __launch_bounds__(kBigBlock)
                 double mp = 0.0;
                 for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
                     const int a = (int)(spk[2 * k] & 0xffffffffu), b = (int)(spk[2 * k + 1] & 0xffffffffu);
-                    const double rwa = A.rw2(a), rwb = A.rw2(b);
+                    const double rwa = A.rw2(a), rwb = A.rw2(b), ra = sqrt(rwa), rb = sqrt(rwb);
                     const unsigned long long Na = A.N(a), Nb = A.N(b);
                     const unsigned long long Nmax = Na > Nb ? Na : Nb;
-                    const double P = prob(p, Nmax, rwa, rwb, geo ? vt_of(p, rwa, nu, cX) : 0.0,
-                                          geo ? vt_of(p, rwb, nu, cX) : 0.0, dtpp, scale);
+                    const double P = prob(p, Nmax, rwa, ra, rwb, rb, geo ? vt_of(p, rwa, ra, nu, cX) : 0.0,
+                                          geo ? vt_of(p, rwb, rb, nu, cX) : 0.0, dtpp, scale);
                     np++;
                     if (P > 1.0) ng++;
                     mp = fmax(mp, P);

@@ -156,9 +156,9 @@ SDM_HD Thermo thermo_eval(double th, double rv, double rhod, double RH_max) {
 }
 
 // Khvorostyanov & Curry (2002) sphere: Re(X), X = cX r^3 (Best number)
-SDM_HD double reynolds(double rw2, double cX) {
+// Re from r_w^2 and r_w = sqrt(r_w^2) (callers that keep r pass it)
+SDM_HD double reynolds_r(double rw2, double r, double cX) {
     using namespace phys;
-    const double r = sqrt(rw2);
     if (!(r > 0.0)) return 0.0;
     const double X = cX * rw2 * r;
     const double c1 = 4.0 / (delta0 * delta0 * sqrt(C0));
@@ -167,12 +167,15 @@ SDM_HD double reynolds(double rw2, double cX) {
     return delta0 * delta0 / 4.0 * s * s;
 }
 
+SDM_HD double reynolds(double rw2, double cX) { return reynolds_r(rw2, sqrt(rw2), cX); }
+
 // terminal velocity v_t = Re nu / (2 r)
-SDM_HD double vterm(double rw2, double nu, double cX) {
-    const double r = sqrt(rw2);
+SDM_HD double vterm_r(double rw2, double r, double nu, double cX) {
     if (!(r > 0.0)) return 0.0;
-    return reynolds(rw2, cX) * nu / (2.0 * r);
+    return reynolds_r(rw2, r, cX) * nu / (2.0 * r);
 }
+
+SDM_HD double vterm(double rw2, double nu, double cX) { return vterm_r(rw2, sqrt(rw2), nu, cX); }
 
 // the same terminal velocity in FP32 (mixed-precision mode)
 SDM_HD float vterm_f(float rw2, float nu, float cX) {
