@@ -57,6 +57,7 @@ class Opts(C.Structure):
     _fields_ = [
         ("adve", C.c_int), ("sedi", C.c_int), ("cond", C.c_int), ("coal", C.c_int),
         ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int),
+        ("coal_multi", C.c_int),
     ]
 
 
@@ -173,7 +174,8 @@ def make_domain(cfg: dict) -> Domain:
 def make_opts(o: dict | None = None) -> Opts:
     o = o or {}
     return Opts(o.get("adve", 1), o.get("sedi", 1), o.get("cond", 1), o.get("coal", 1),
-                o.get("RH_max", 44.0), o.get("sstp_cond", 10), o.get("sstp_coal", 10))
+                o.get("RH_max", 44.0), o.get("sstp_cond", 10), o.get("sstp_coal", 10),
+                o.get("coal_multi", 0))
 
 
 def thermo(th, rv, rhod, RH_max=44.0) -> Thermo:

@@ -639,22 +639,44 @@ static double kernel_K(const orc_domain *d, const orc_thermo *t, double rw2a, do
     return PI * (ra + rb) * (ra + rb) * dv;
 }
 
-/* One collision event of all min(N_i, N_j) particles (Sec. 5.1.4).  READING
- * of the garbled role assignment: the super-droplet with the larger
- * multiplicity (the first of the pair on a tie) keeps its radii and loses
- * the other's multiplicity; the other keeps its multiplicity and takes the
- * merged radii: r_w^3 and r_d^3 summed, kappa averaged weighted by r_d^3. */
-static void collide(orc_sds *s, int64_t a, int64_t b)
+/* gamma collision events of all min(N_i, N_j) particles (Sec. 5.1.4; gamma
+ * is 1 unless multiple coalescence is on).  READING of the garbled role
+ * assignment: the super-droplet with the larger multiplicity L (the first
+ * of the pair on a tie) keeps its radii and loses gamma times the other's
+ * multiplicity; the other, S, keeps its multiplicity and takes the merged
+ * radii: r_w^3 and r_d^3 of gamma L-droplets added to its own, kappa
+ * averaged weighted by r_d^3. */
+static void collide(orc_sds *s, int64_t a, int64_t b, uint64_t gamma)
 {
     int64_t L = s->N[a] >= s->N[b] ? a : b;
     int64_t S = L == a ? b : a;
-    s->N[L] -= s->N[S];
-    double r3 = s->rw2[S] * sqrt(s->rw2[S]) + s->rw2[L] * sqrt(s->rw2[L]);
+    s->N[L] -= gamma * s->N[S];
+    double g = (double)gamma;
+    double r3 = s->rw2[S] * sqrt(s->rw2[S]) + g * (s->rw2[L] * sqrt(s->rw2[L]));
     double r = cbrt(r3);
     s->rw2[S] = r * r;
-    double m3 = s->rd3[S] + s->rd3[L];
-    if (m3 > 0.0) s->kappa[S] = (s->kappa[S] * s->rd3[S] + s->kappa[L] * s->rd3[L]) / m3;
+    double dL = g * s->rd3[L];
+    double m3 = s->rd3[S] + dL;
+    if (m3 > 0.0) s->kappa[S] = (s->kappa[S] * s->rd3[S] + s->kappa[L] * dL) / m3;
     s->rd3[S] = m3;
+}
+
+/* Number of collision events of a pair with scaled probability P and
+ * uniform number u.  The paper's scheme (Sec. 5.1.4): one event when u < P,
+ * whatever P.  Multiple coalescence (Shima et al. 2009, Sec. 4.1.4 there),
+ * which the paper plans for P > 1: gamma = floor(P), plus one when
+ * u < P - floor(P), so that E[gamma] = P; at most floor(N_L/N_S) events can
+ * take place. */
+static uint64_t n_events(double P, double u, uint64_t NL, uint64_t NS, int multi)
+{
+    if (!multi) return u < P ? 1 : 0;
+    if (!(P > 0.0)) return 0;
+    uint64_t cap = NL / NS;
+    double fl = floor(P);
+    if (fl >= (double)cap) return cap;
+    uint64_t g = (uint64_t)fl;
+    if (u < P - fl) g++;
+    return g < cap ? g : cap;
 }
 
 /* sstp_coal substeps per cell.  In each: the cell's n super-droplets with
@@ -695,14 +717,16 @@ void orc_coalesce(const orc_domain *d, const orc_opts *o, orc_sds *s, const doub
                 int64_t a = buf[2 * k].i, b = buf[2 * k + 1].i;
                 double K = kernel_K(d, &t, s->rw2[a], s->rw2[b]);
                 uint64_t Nmax = s->N[a] > s->N[b] ? s->N[a] : s->N[b];
+                uint64_t Nmin = s->N[a] > s->N[b] ? s->N[b] : s->N[a];
                 double P = (double)Nmax * K * dtpp / dV * scale;
                 if (st) {
                     st->n_pairs++;
                     if (P > 1.0) st->n_pgt1++;
                     if (P > st->max_p) st->max_p = P;
                 }
-                if (orc_u01(buf[2 * k].acc) < P) {
-                    collide(s, a, b);
+                uint64_t gamma = n_events(P, orc_u01(buf[2 * k].acc), Nmax, Nmin, o->coal_multi);
+                if (gamma > 0) {
+                    collide(s, a, b, gamma);
                     if (st) st->n_coll++;
                 }
             }

@@ -44,6 +44,7 @@ typedef struct {
     int adve, sedi, cond, coal;
     double RH_max;
     int sstp_cond, sstp_coal;
+    int coal_multi;                /* 1: multiple coalescence for P_ij > 1      */
 } orc_opts;
 
 typedef struct {

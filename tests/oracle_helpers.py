@@ -26,10 +26,11 @@ def make_state(N, rw2, rd3=None, kappa=None, uid=None, x=None, y=None, z=None):
     return s
 
 
-def coalesce(cfg, state, step=0, sstp=1, th=300.0, rv=0.01, rhod=1.0):
-    """One orc_coalesce call on ``state`` (modified in place); returns stats."""
+def coalesce(cfg, state, step=0, sstp=1, th=300.0, rv=0.01, rhod=1.0, multi=0):
+    """One orc_coalesce call on ``state`` (modified in place); returns stats.
+    ``multi`` turns on multiple coalescence for P > 1."""
     dom = oracle.make_domain(cfg)
-    o = oracle.make_opts(dict(adve=0, sedi=0, cond=0, coal=1, sstp_coal=sstp))
+    o = oracle.make_opts(dict(adve=0, sedi=0, cond=0, coal=1, sstp_coal=sstp, coal_multi=multi))
     nc = int(oracle.lib().orc_n_cells(C.byref(dom)))
     f = lambda v: np.full(nc, v, np.float64)
     TH, RV, RD = f(th), f(rv), f(rhod)
