@@ -58,14 +58,18 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cells", type=int, default=128, help="updraft_3d: cells per dimension")
+    ap.add_argument("--diag", action="store_true",
+                    help="also run the diagnostics after every step (moments k = 0..3 and a 64-bin spectrum of "
+                         "the wet radius), as an output step of a model would; off for the headline number")
     return ap.parse_args()
 
 
-def make_workload(name: str, seed: int):
+def make_workload(name: str, seed: int, cells: int = 128):
     if name == "icmw_2d":
         return workloads.icmw_2d(seed=seed)
     if name == "updraft_3d":
-        return workloads.updraft_3d(seed=seed)
+        return workloads.updraft_3d(nx=cells, ny=cells, nz=cells, seed=seed)
     return workloads.golovin_box(seed=seed)
 
 
@@ -134,7 +138,7 @@ def run_gpu(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    w = make_workload(args.workload, seed=rank)
+    w = make_workload(args.workload, seed=rank, cells=args.cells)
     opts = w.opts
     if args.workload == "golovin_box":
         opts = dict(w.opts)
@@ -146,11 +150,21 @@ def run_gpu(args, rank: int, world: int):
     p = sdm.Particles(w.cfg, th, rv, rhod, *Cs, stream=stream.cuda_stream, precision=args.precision)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    edges = np.geomspace(1e-9, 1e-2, 65)
+    spec = torch.empty((64, p.n_cells), dtype=torch.float64, device="cuda") if args.diag else None
+    mom = torch.empty(p.n_cells, dtype=torch.float64, device="cuda") if args.diag else None
+
     def step():
         if opts.get("cond", 1):
             p.step_sync(opts, th, rv)
         p.step_async(opts)
         p.wait()
+        if args.diag:
+            sdm.sdm_diag_rng(p.ctx, True, 0.0, 1.0)
+            for k in range(4):
+                sdm.sdm_diag_mom(p.ctx, k)
+                sdm.sdm_outbuf(p.ctx, mom)
+            sdm.sdm_diag_spectrum(p.ctx, True, edges, 3, spec)
 
     for _ in range(args.warmup):
         step()
@@ -333,12 +347,12 @@ def whole_job_value(n_sd_per_rank: int, steps: int, world: int, t_max: float) ->
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample(steps: int, warmup: int):
+def oracle_sample(steps: int, warmup: int, nx: int = 4):
     """The CPU oracle as it stands on a bounded sample of the workload: the
-    same 2D case restricted to 4 of the 75 columns (4 x 75 cells, 64 SD/cell,
-    19 200 SDs), full steps; single thread."""
+    same 2D case restricted to nx of the 75 columns (nx x 75 cells, 64
+    SD/cell), full steps; single thread."""
     import oracle
-    w = workloads.icmw_2d(nx=4)
+    w = workloads.icmw_2d(nx=nx)
     o = oracle.Oracle(w.cfg)
     o.init(w.th, w.rv, w.rhod)
     for _ in range(warmup):
@@ -371,7 +385,8 @@ def main():
 
     if args.impl == "reference":
         if rank == 0:
-            v, n_sd, dt = oracle_sample(max(1, args.steps // 10), min(1, args.warmup))
+            # every step a bounded sample of the workload: 4 of its 75 columns
+            v, n_sd, dt = oracle_sample(args.steps, args.warmup)
             w = make_workload(args.workload, 0)
             line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                         warmup=args.warmup, ms_per_step=w.n_sd / v * 1e3, higher_is_better=True,
@@ -379,7 +394,8 @@ def main():
                         config=workload_desc(w),
                         cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle",
                                           sample=f"2D case, 4x75 cells x 64 SD ({n_sd} SDs), "
-                                                 f"{max(1, args.steps // 10)} full steps, {dt:.1f} s"),
+                                                 f"{args.steps} full steps after {args.warmup} warm-up, "
+                                                 f"{dt:.1f} s, serial"),
                         e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
             print(json.dumps(line), flush=True)
         if world > 1:
@@ -477,9 +493,9 @@ def main():
                            d2h_bytes_per_step=res["d2h"])
     if not args.no_cpu:
         try:
-            v, n_sd, dt = oracle_sample(2, 1)
+            v, n_sd, dt = oracle_sample(8, 1, nx=8)
             line["cpu_baseline"] = dict(value=v, unit=UNIT, cores=1, kind="oracle",
-                                        sample=f"2D case, 4x75 cells x 64 SD ({n_sd} SDs), 2 full steps "
+                                        sample=f"2D case, 8x75 cells x 64 SD ({n_sd} SDs), 8 full steps "
                                                f"after 1 warm-up, {dt:.1f} s, serial")
         except Exception as e:  # the oracle is a baseline, never a fallback
             line["cpu_baseline"] = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample=f"failed: {e}")

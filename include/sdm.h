@@ -106,12 +106,20 @@ typedef struct {
     int cond_solver;
 } sdm_opts_init;
 
-/* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10):
- * process toggles, RH limit for drop growth, substep counts. */
+/* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10, 0):
+ * process toggles, RH limit for drop growth, substep counts.
+ * coal_multi = 0 is the paper's scheme: a pair with P_ij > 1 still has one
+ * collision event (Sec. 5.1.4).  coal_multi = 1 turns on the multiple
+ * coalescence that Sec. 5.1.4 plans (Shima et al. 2009, Sec. 4.1.4 there):
+ * gamma = floor(P_ij) events, plus one when the pair's uniform number is
+ * below P_ij - floor(P_ij), at most floor(N_L / N_S); the merged droplet
+ * takes gamma droplets of the larger-multiplicity super-droplet.  Where
+ * every P_ij <= 1 both give the same result bit for bit. */
 typedef struct {
     int adve, sedi, cond, coal;
     double RH_max;
     int sstp_cond, sstp_coal;
+    int coal_multi;
 } sdm_opts;
 
 /* Counters accumulated since sdm_init (or the last sdm_stats_reset). */
@@ -200,6 +208,21 @@ sdm_status sdm_diag_sd_conc(sdm_ctx *ctx);
 /* Copy the output buffer (n_cells float64, row-major (x, y, z)) to dst,
  * host (dst_on_device = 0, complete on return) or device memory. */
 sdm_status sdm_outbuf(sdm_ctx *ctx, double *dst, int dst_on_device);
+
+/* Binned spectrum: the moment of sdm_diag_mom (Sec. 5.2.1) for n_bins
+ * radius bins in one pass,
+ *   dst[b * n_cells + c] = (rho_d dV)^-1 sum N r^k
+ * over the super-droplets of cell c whose wet (wet = 1) or dry (wet = 0)
+ * radius lies in [edges[b], edges[b+1]) (half-open: a radius falls in at
+ * most one bin).  edges: host array of n_bins + 1 strictly increasing radii
+ * [m]; 1 <= n_bins <= 256; 0 <= k <= 8 (SDM_EINVAL otherwise).  dst:
+ * n_bins * n_cells float64, bin-major, in host memory (dst_on_device = 0;
+ * complete on return) or device memory (ordered on the context's stream).
+ * Leaves the output buffer and the sdm_diag_rng selection untouched.  A
+ * call with more bins than every earlier one allocates the context's
+ * spectrum buffer (n_bins * n_cells float64), kept until sdm_destroy. */
+sdm_status sdm_diag_spectrum(sdm_ctx *ctx, int wet, const double *edges, int n_bins, int k, double *dst,
+                             int dst_on_device);
 
 /* ---- state access (tests, checkpoint / resume) --------------------------- */
 

@@ -124,6 +124,7 @@ def lib():
             L.orc_step_async.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D),
                                          _P(_D), _P(_D), _P(_D), C.c_uint64, _P(Stats)]
             L.orc_moments.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _D, _D, C.c_int, _P(_D)]
+            L.orc_spectrum.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _P(_D), C.c_int, C.c_int, _P(_D)]
             L.orc_sd_conc.argtypes = [_P(Domain), _P(SDs), _P(_D)]
             _lib = L
     return _lib
@@ -292,6 +293,15 @@ class Oracle:
         s = self.state.struct()
         lib().orc_moments(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), r_min, r_max, k, _dp(out))
         return out
+
+    def spectrum(self, wet: bool, edges, k: int):
+        """Moment k in each radius bin [edges[b], edges[b+1]): (n_bins, n_cells)."""
+        edges = np.ascontiguousarray(edges, np.float64)
+        nb = len(edges) - 1
+        out = np.zeros(nb * self.n_cells)
+        s = self.state.struct()
+        lib().orc_spectrum(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), _dp(edges), nb, k, _dp(out))
+        return out.reshape(nb, self.n_cells)
 
     def sd_conc(self):
         out = np.zeros(self.n_cells)

@@ -773,6 +773,29 @@ void orc_moments(const orc_domain *d, const orc_sds *s, const double *rhod, int 
     for (int64_t c = 0; c < nc; ++c) out[c] /= rhod[c] * dV;
 }
 
+/* Binned spectrum: the moment M^k of the diagnostics above for each of the
+ * n_bins radius bins [edges[b], edges[b+1]) (READING: half-open, so that
+ * every radius falls in at most one bin), out[b * n_cells + c]. */
+void orc_spectrum(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
+                  const double *edges, int n_bins, int k, double *out)
+{
+    int64_t nc = orc_n_cells(d);
+    double dV = cell_volume(d);
+    for (int64_t i = 0; i < nc * n_bins; ++i) out[i] = 0.0;
+    for (int64_t q = 0; q < s->n; ++q) {
+        double r = wet ? sqrt(s->rw2[q]) : cbrt(s->rd3[q]);
+        int b = -1;
+        for (int e = 0; e < n_bins; ++e)
+            if (r >= edges[e] && r < edges[e + 1]) b = e;
+        if (b < 0) continue;
+        double p = 1.0;
+        for (int e = 0; e < k; ++e) p *= r;
+        out[b * nc + orc_cell_of(d, s->x[q], s->y[q], s->z[q])] += (double)s->N[q] * p;
+    }
+    for (int b = 0; b < n_bins; ++b)
+        for (int64_t c = 0; c < nc; ++c) out[b * nc + c] /= rhod[c] * dV;
+}
+
 /* READING: super-droplet "concentration" is the count of super-droplets with
  * non-zero multiplicity in each cell. */
 void orc_sd_conc(const orc_domain *d, const orc_sds *s, double *out)

@@ -106,5 +106,7 @@ void orc_step_async(const orc_domain *d, const orc_opts *o, orc_sds *s, const do
 void orc_moments(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
                  double r_min, double r_max, int k, double *out);
 void orc_sd_conc(const orc_domain *d, const orc_sds *s, double *out);
+void orc_spectrum(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
+                  const double *edges, int n_bins, int k, double *out);
 
 #endif

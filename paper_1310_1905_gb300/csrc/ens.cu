@@ -294,6 +294,7 @@ struct EnsCoalParams {
     double dt;
     int sstp, kernel, mixed;
     double golovin_b;
+    int multi;
 };
 
 // sort keys of one coalescence substep: word 0 of the pairing draw (its
@@ -356,7 +357,6 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
             const unsigned long long Na = s.N[a], Nb = s.N[b];
             const unsigned long long Nmax = Na > Nb ? Na : Nb;
             double P;
-            bool acc_ok;
             struct {
                 double nu, cX;
             } t{md.nu, md.cX};
@@ -373,7 +373,6 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
                 }
                 const float Pf = (float)Nmax * K * (float)dtpp / (float)md.dV * (float)scale;
                 P = Pf;
-                acc_ok = u01f(acc[a]) < Pf;
             } else {
                 double K;
                 if (p.kernel == SDM_KERNEL_GOLOVIN) {
@@ -386,19 +385,21 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
                     K = phys::pi * (ra + rb) * (ra + rb) * dv;
                 }
                 P = (double)Nmax * K * dtpp / md.dV * scale;
-                acc_ok = u01(acc[a]) < P;
             }
+            const unsigned long long gam = n_events(P, acc[a], Nmax, Na > Nb ? Nb : Na, p.multi, p.mixed);
             npair = 1;
             ngt1 = P > 1.0;
             mp = P;
-            if (acc_ok) {
+            if (gam) {  // gamma events, as collide() in the single-context kernels
                 const uint32_t L = Na >= Nb ? a : b, S = L == a ? b : a;
-                s.N[L] -= s.N[S];
-                if (Na == Nb) atomicAdd(&M[m].zeros, 1u);  // recycled at the next step
+                const unsigned long long NS = s.N[S];
+                s.N[L] -= gam * NS;
+                if (s.N[L] == 0) atomicAdd(&M[m].zeros, 1u);  // recycled at the next step
+                const double g = (double)gam;
                 const double rwS = s.rw2[S], rwL = s.rw2[L];
-                const double r = cbrt(rwS * sqrt(rwS) + rwL * sqrt(rwL));
+                const double r = cbrt(rwS * sqrt(rwS) + g * (rwL * sqrt(rwL)));
                 s.rw2[S] = r * r;
-                const double dS = s.rd3[S], dL = s.rd3[L], m3 = dS + dL;
+                const double dS = s.rd3[S], dL = g * s.rd3[L], m3 = dS + dL;
                 if (m3 > 0.0) s.kappa[S] = (s.kappa[S] * dS + s.kappa[L] * dL) / m3;
                 s.rd3[S] = m3;
                 ncoll = 1;
@@ -610,7 +611,7 @@ sdm_status enqueue_step(sdm_ens *e, const sdm_opts &o) {
         }
     }
     if (o.coal) {
-        EnsCoalParams p{e->eo.dt, o.sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b};
+        EnsCoalParams p{e->eo.dt, o.sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b, o.coal_multi ? 1 : 0};
         const int ab = aux_bytes_for(nm);
         k_ens_ambient<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
         const int64_t n = e->n_sd;
@@ -865,6 +866,12 @@ sdm_status sdm_ens_members(const sdm_ens *e, int32_t *ids, int32_t cap, int32_t 
     return SDM_OK;
 }
 
+// field by field: a caller's struct may carry any bytes in its padding
+static bool same_opts(const sdm_opts &a, const sdm_opts &b) {
+    return a.adve == b.adve && a.sedi == b.sedi && a.cond == b.cond && a.coal == b.coal && a.RH_max == b.RH_max &&
+           a.sstp_cond == b.sstp_cond && a.sstp_coal == b.sstp_coal && a.coal_multi == b.coal_multi;
+}
+
 sdm_status sdm_ens_step(sdm_ens *e, const sdm_opts *o, const int32_t *ids, const double *rhod, int32_t n) {
     if (!e || !o) return efail(e, SDM_EINVAL, "NULL argument");
     if (e->in_flight) return efail(e, SDM_ESTATE, "step before sdm_ens_wait of the previous one");
@@ -879,7 +886,7 @@ sdm_status sdm_ens_step(sdm_ens *e, const sdm_opts *o, const int32_t *ids, const
         e->rhod_pin[m] = rhod[k];
     }
     if (e->use_graph) {
-        const bool same = e->graph && memcmp(&e->graph_opts, o, sizeof(sdm_opts)) == 0;
+        const bool same = e->graph && same_opts(e->graph_opts, *o);
         if (!same) {
             if (e->graph) cudaGraphExecDestroy(e->graph);
             e->graph = nullptr;

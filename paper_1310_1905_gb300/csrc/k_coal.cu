@@ -10,7 +10,8 @@
 // Philox key (ties by id) and paired (0,1), (2,3), ...; pair k collides when
 // its scaled probability, eq. (P_ij),
 //     P = max(N_i, N_j) K(r_i, r_j) dt''/dV * n (n-1) / (2 floor(n/2)),
-// exceeds the uniform number drawn for the pair's first member.
+// exceeds the uniform number drawn for the pair's first member (with
+// multiple coalescence on, floor(P) or floor(P) + 1 events: n_events).
 //
 // Cells of up to 64 super-droplets: one warp each, two per lane, a
 // register bitonic sort through shuffles and per-warp shared memory for the
@@ -22,7 +23,7 @@ namespace sdm {
 
 struct CoalParams {
     Grid g;
-    int sstp, coal, kernel, mixed;
+    int sstp, coal, kernel, mixed, multi;
     double golovin_b;
     uint64_t seed, step;
 };
@@ -128,28 +129,27 @@ __device__ __forceinline__ double prob(const CoalParams &p, unsigned long long N
     return (double)Nmax * K * dtpp / p.g.dV * scale;
 }
 
-__device__ __forceinline__ bool accepted(const CoalParams &p, uint64_t w, double P) {
-    return p.mixed ? u01f(w) < (float)P : u01(w) < P;
-}
-
 // mixed precision sorts on the 31 leading bits of the draw (ties fall back
 // to id order), the key width the batched ensemble sorts on
 __device__ __forceinline__ unsigned long long key_of(const CoalParams &p, uint64_t w0) {
     return p.mixed ? (w0 & 0xFFFFFFFE00000000ull) : w0;
 }
 
-// one collision event: the larger-N member (the first on a tie) keeps its
-// radii and loses the other's N; the other takes the merged droplet
-// (r_w^3, r_d^3 summed, kappa weighted by r_d^3).  Returns the merged slot.
+// gamma collision events (gamma = 1 in the paper's scheme): the larger-N
+// member L (the first on a tie) keeps its radii and loses gamma times the
+// other's N; the other takes the merged droplet (r_w^3 and r_d^3 of gamma
+// L-droplets added to its own, kappa weighted by r_d^3).  Returns the
+// merged slot.
 template <class Acc>
-__device__ __forceinline__ int collide(Acc &A, int a, int b) {
+__device__ __forceinline__ int collide(Acc &A, int a, int b, unsigned long long gamma) {
     const int L = A.N(a) >= A.N(b) ? a : b;
     const int S = L == a ? b : a;
-    A.setN(L, A.N(L) - A.N(S));
-    const double r3 = A.rw2(S) * A.r(S) + A.rw2(L) * A.r(L);
+    A.setN(L, A.N(L) - gamma * A.N(S));
+    const double g = (double)gamma;
+    const double r3 = A.rw2(S) * A.r(S) + g * (A.rw2(L) * A.r(L));
     const double r = cbrt(r3);
     A.setrw2(S, r * r);
-    const double dS = A.rd3(S), dL = A.rd3(L);
+    const double dS = A.rd3(S), dL = g * A.rd3(L);
     const double m3 = dS + dL;
     if (m3 > 0.0) A.setkappa(S, (A.kappa(S) * dS + A.kappa(L) * dL) / m3);
     A.setrd3(S, m3);
@@ -275,14 +275,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 const bool mine = R >= 2 || (lane & 1) == 0;
                 if (mine && pos + 1 < m) {
                     const int a = (int)(ka.pk & 0xffu), b = (int)(kb.pk & 0xffu);
-                    const unsigned long long Nmax = W.N[a] > W.N[b] ? W.N[a] : W.N[b];
+                    const unsigned long long Na = W.N[a], Nb = W.N[b];
+                    const unsigned long long Nmax = Na > Nb ? Na : Nb, Nmin = Na > Nb ? Nb : Na;
                     const double P = prob(p, Nmax, W.rw2[a], W.r[a], W.rw2[b], W.r[b], W.vt[a], W.vt[b], dtpp,
                                           scale);
                     n_pairs++;
                     if (P > 1.0) n_pgt1++;
                     max_p = fmax(max_p, P);
-                    if (accepted(p, W.acc[a], P)) {
-                        const int S = collide(A, a, b);
+                    const unsigned long long gam = n_events(P, W.acc[a], Nmax, Nmin, p.multi, p.mixed);
+                    if (gam) {
+                        const int S = collide(A, a, b, gam);
                         if (geo) W.vt[S] = vt_of(p, W.rw2[S], W.r[S], nu, cX);
                         n_coll++;
                     }
@@ -439,14 +441,15 @@ __global__ void __launch_bounds__(kBigBlock)
                     const int a = (int)(spk[2 * k] & 0xffffffffu), b = (int)(spk[2 * k + 1] & 0xffffffffu);
                     const double rwa = A.rw2(a), rwb = A.rw2(b), ra = sqrt(rwa), rb = sqrt(rwb);
                     const unsigned long long Na = A.N(a), Nb = A.N(b);
-                    const unsigned long long Nmax = Na > Nb ? Na : Nb;
+                    const unsigned long long Nmax = Na > Nb ? Na : Nb, Nmin = Na > Nb ? Nb : Na;
                     const double P = prob(p, Nmax, rwa, ra, rwb, rb, geo ? vt_of(p, rwa, ra, nu, cX) : 0.0,
                                           geo ? vt_of(p, rwb, rb, nu, cX) : 0.0, dtpp, scale);
                     np++;
                     if (P > 1.0) ng++;
                     mp = fmax(mp, P);
-                    if (accepted(p, sacc[a], P)) {
-                        collide(A, a, b);
+                    const unsigned long long gam = n_events(P, sacc[a], Nmax, Nmin, p.multi, p.mixed);
+                    if (gam) {
+                        collide(A, a, b, gam);
                         nc++;
                     }
                 }
@@ -479,6 +482,7 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     p.coal = coal ? 1 : 0;
     p.kernel = c->oi.kernel;
     p.mixed = c->oi.precision == SDM_PRECISION_MIXED;
+    p.multi = o.coal_multi ? 1 : 0;
     p.golovin_b = c->oi.golovin_b;
     p.seed = c->oi.seed;
     p.step = c->step;

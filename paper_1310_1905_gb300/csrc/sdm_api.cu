@@ -212,6 +212,8 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->rhod);
     cudaFree(c->amb);
     cudaFree(c->outbuf);
+    cudaFree(c->spec_buf);
+    cudaFree(c->spec_edges);
     for (int d = 0; d < 3; ++d) cudaFree(c->rhoC[d]);
     cudaFree(c->scan_tmp);
     cudaFree(c->rc_tmp);
@@ -628,6 +630,39 @@ sdm_status sdm_diag_sd_conc(sdm_ctx *c) {
     Phase ph(c, PH_DIAG);
     CK(launch_sd_conc(c), "sd_conc");
     c->tacc.launches += 1;
+    return SDM_OK;
+}
+
+sdm_status sdm_diag_spectrum(sdm_ctx *c, int wet, const double *edges, int n_bins, int k, double *dst,
+                             int dst_on_device) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (!edges || !dst) return fail(c, SDM_EINVAL, "NULL argument");
+    if (n_bins < 1 || n_bins > sdm::kMaxSpectrumBins) return fail(c, SDM_EINVAL, "n_bins must be 1..256");
+    if (k < 0 || k > 8) return fail(c, SDM_EINVAL, "moment order must be 0..8");
+    for (int b = 0; b < n_bins; ++b)
+        if (!(edges[b] < edges[b + 1])) return fail(c, SDM_EINVAL, "bin edges must increase strictly");
+    if (c->layout_dirty)
+        if (sdm_status s = regroup(c)) return s;
+    if (n_bins > c->spec_cap) {
+        CK(cudaStreamSynchronize(c->stream), "spectrum buffer");
+        cudaFree(c->spec_buf);
+        c->spec_buf = nullptr;
+        c->spec_cap = 0;
+        CK(cudaMalloc(&c->spec_buf, sizeof(double) * (size_t)n_bins * (size_t)c->grid.n_cells), "spectrum buffer");
+        if (!c->spec_edges)
+            CK(cudaMalloc(&c->spec_edges, sizeof(double) * (sdm::kMaxSpectrumBins + 1)), "spectrum buffer");
+        c->spec_cap = n_bins;
+    }
+    Phase ph(c, PH_DIAG);
+    CK(cudaMemcpyAsync(c->spec_edges, edges, sizeof(double) * (size_t)(n_bins + 1), cudaMemcpyHostToDevice,
+                       c->stream),
+       "spectrum edges");
+    CK(launch_spectrum(c, wet ? 1 : 0, n_bins, k), "spectrum");
+    c->tacc.launches += 1;
+    CK(cudaMemcpyAsync(dst, c->spec_buf, sizeof(double) * (size_t)n_bins * (size_t)c->grid.n_cells,
+                       dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+       "spectrum copy");
+    if (!dst_on_device) CK(cudaStreamSynchronize(c->stream), "spectrum copy");
     return SDM_OK;
 }
 

@@ -192,6 +192,25 @@ SDM_HD float vterm_f(float rw2, float nu, float cX) {
 // 24 random bits plus one half, times 2^-24: open (0,1) in FP32
 SDM_HD float u01f(uint64_t v) { return ((float)(uint32_t)(v >> 40) + 0.5f) * 5.9604645e-8f; }
 
+// Collision events of a pair with scaled probability P (eq. P_ij), uniform
+// draw w and multiplicities NL >= NS > 0.  The paper's scheme (Sec. 5.1.4):
+// one event when u < P.  Multiple coalescence (multi = 1; Shima et al.
+// 2009): floor(P), plus one when u < P - floor(P) (exact in either
+// precision for P >= 1), at most floor(NL / NS).  Below P = 1 both are the
+// single test u < P, so the 64-bit division is only taken for P >= 1.  In
+// mixed precision P holds an FP32 value and the test uses the 24-bit draw.
+__device__ __forceinline__ unsigned long long n_events(double P, uint64_t w, unsigned long long NL,
+                                                       unsigned long long NS, int multi, int mixed) {
+    const bool hit = mixed ? u01f(w) < (float)P : u01(w) < P;
+    if (!multi || !(P >= 1.0)) return hit ? 1ull : 0ull;
+    const unsigned long long cap = NL / NS;
+    const double fl = floor(P);
+    if (fl >= (double)cap) return cap;
+    unsigned long long g = (unsigned long long)fl;
+    if (mixed ? u01f(w) < (float)P - (float)fl : u01(w) < P - fl) g++;
+    return g < cap ? g : cap;
+}
+
 SDM_HD double fuchs_sutugin(double Kn) {
     return (1.0 + Kn) / (1.0 + (4.0 / 3.0 + 0.377) * Kn + 4.0 / 3.0 * Kn * Kn);
 }
@@ -288,6 +307,8 @@ struct sdm_ctx {
     bool rng_set = false;
     int diag_wet = 1;
     double diag_rmin = 0.0, diag_rmax = 0.0;
+    double *spec_buf = nullptr, *spec_edges = nullptr;  // binned spectrum: n_bins x n_cells, n_bins + 1
+    int spec_cap = 0;                                   // bins spec_buf holds
     uint64_t step = 0;
     uint64_t known_zeros = 0;
     std::string err;
@@ -311,6 +332,8 @@ cudaError_t launch_recycle_compact(sdm_ctx *c);
 cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
 cudaError_t launch_moments(sdm_ctx *c, int k);
 cudaError_t launch_sd_conc(sdm_ctx *c);
+constexpr int kMaxSpectrumBins = 256;
+cudaError_t launch_spectrum(sdm_ctx *c, int wet, int n_bins, int k);
 cudaError_t launch_field_gather(double *dst, const double *src, const int64_t *strides, int ndim,
                                 const int *shape, cudaStream_t s);
 cudaError_t launch_field_scatter(double *dst, const double *src, const int64_t *strides,

@@ -56,7 +56,8 @@ class sdm_opts_init(C.Structure):
 
 class sdm_opts(C.Structure):
     _fields_ = [("adve", C.c_int), ("sedi", C.c_int), ("cond", C.c_int), ("coal", C.c_int),
-                ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int)]
+                ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int),
+                ("coal_multi", C.c_int)]
 
 
 class sdm_stats(C.Structure):
@@ -78,7 +79,7 @@ class sdm_timing(C.Structure):
 
 
 SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_step_async", "sdm_wait",
-           "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
+           "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
            "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc"]
 
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = True):
     L.sdm_diag_mom.argtypes = [ctx, C.c_int]
     L.sdm_diag_sd_conc.argtypes = [ctx]
     L.sdm_outbuf.argtypes = [ctx, V, C.c_int]
+    L.sdm_diag_spectrum.argtypes = [ctx, C.c_int, P(C.c_double), C.c_int, C.c_int, V, C.c_int]
     L.sdm_sizes.argtypes = [ctx, P(I64), P(I64)]
     L.sdm_get_attr.argtypes = [ctx, C.c_int, V, I64]
     L.sdm_set_attr.argtypes = [ctx, C.c_int, V, I64]
@@ -175,7 +177,8 @@ def make_opts_init(cfg: dict, precision: str = "fp64", backend: str = "cuda"):
 def make_opts(d: dict | None = None) -> sdm_opts:
     d = d or {}
     return sdm_opts(d.get("adve", 1), d.get("sedi", 1), d.get("cond", 1), d.get("coal", 1),
-                    d.get("RH_max", 44.0), d.get("sstp_cond", 10), d.get("sstp_coal", 10))
+                    d.get("RH_max", 44.0), d.get("sstp_cond", 10), d.get("sstp_coal", 10),
+                    d.get("coal_multi", 0))
 
 
 def _check(L, ctx, status):
@@ -252,6 +255,25 @@ def sdm_outbuf(ctx, out=None):
         _check(L, ctx, L.sdm_outbuf(ctx, out.ctypes.data, 0))
     else:
         _check(L, ctx, L.sdm_outbuf(ctx, out.data_ptr(), 1))
+    return out
+
+
+def sdm_diag_spectrum(ctx, wet: bool, edges, k: int, out=None):
+    """Moment k per cell in every radius bin [edges[b], edges[b+1]) into
+    ``out`` (numpy host array or torch CUDA tensor of (n_bins, n_cells)
+    float64); returns it."""
+    L = load()
+    e = np.ascontiguousarray(edges, np.float64)
+    nb = len(e) - 1
+    if out is None:
+        out = np.empty((nb, sdm_sizes(ctx)[1]), np.float64)
+    ep = e.ctypes.data_as(C.POINTER(C.c_double))
+    if isinstance(out, np.ndarray):
+        assert out.flags.c_contiguous and out.dtype == np.float64 and out.size == nb * sdm_sizes(ctx)[1]
+        _check(L, ctx, L.sdm_diag_spectrum(ctx, int(wet), ep, nb, k, out.ctypes.data, 0))
+    else:
+        assert out.is_contiguous() and out.numel() == nb * sdm_sizes(ctx)[1]
+        _check(L, ctx, L.sdm_diag_spectrum(ctx, int(wet), ep, nb, k, out.data_ptr(), 1))
     return out
 
 
@@ -357,6 +379,9 @@ class Particles:
     def diag_sd_conc(self):
         sdm_diag_sd_conc(self.ctx)
         return sdm_outbuf(self.ctx)
+
+    def diag_spectrum(self, wet: bool, edges, k: int):
+        return sdm_diag_spectrum(self.ctx, wet, edges, k)
 
     def attr(self, name):
         return sdm_get_attr(self.ctx, name)

@@ -152,3 +152,31 @@ def test_full_size_invariants(name):
     assert (N1 * g["rw2"] ** 1.5).sum() == pytest.approx(w3, rel=1e-12)
     assert (N1 * g["rd3"]).sum() == pytest.approx(d3, rel=1e-12)
     assert p.stats()["n_coll"] > 0
+
+
+@pytest.mark.parametrize("name", ["icmw_2d", "updraft_3d"])
+def test_full_size_spectrum(name):
+    """Any size: the binned spectrum of the library's own state equals the
+    host's binning of that state (np.digitize, half-open bins) in sampled
+    cells, and over bins that cover every radius it sums, per cell, to the
+    moment over the whole range."""
+    w = workload(name)
+    per_cell = w.cfg["sd_conc"]
+    dV = w.cfg["dx"] * w.cfg["dy"] * w.cfg["dz"]
+    rhod = np.ascontiguousarray(w.rhod).ravel()
+    p = gpu_particles(w)
+    th, rv = np.ascontiguousarray(w.th).copy(), np.ascontiguousarray(w.rv).copy()
+    p.step_sync(COND, th, rv)
+    edges = np.geomspace(1e-9, 1e-2, 65)
+    spec = p.diag_spectrum(True, edges, 3)
+    assert spec.shape == (64, w.n_cells)
+    np.testing.assert_allclose(spec.sum(axis=0), p.diag_moments(True, 0.0, 1.0, 3), rtol=1e-12)
+    uid, g = by_uid(p, ["N", "rw2"])
+    cell = uid // per_cell  # no transport: every super-droplet is in its initial cell
+    r = np.sqrt(g["rw2"])
+    b = np.digitize(r, edges) - 1
+    rng = np.random.default_rng(2)
+    for c in rng.choice(w.n_cells, size=32, replace=False):
+        m = cell == c
+        ref = np.bincount(b[m], weights=g["N"][m].astype(float) * r[m] ** 3, minlength=64) / (rhod[c] * dV)
+        assert_close(f"spectrum of cell {c}", spec[:, c], ref, atol=1e-300)

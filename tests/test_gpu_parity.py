@@ -276,3 +276,33 @@ def test_status_codes():
     bad = dict(w.cfg, sd_conc=0)
     with pytest.raises(sdm.SdmError):
         sdm.sdm_init(bad, w.th, w.rv, w.rhod)
+
+
+def test_spectrum_matches_oracle():
+    """Binned spectrum (one pass over all bins) against the oracle's, after
+    some condensation; log-spaced bins, a single bin, and bins that leave
+    part of the spectrum out.  Also into device memory, and the moments of
+    diag_mom are left as they were."""
+    w = small_2d(13)
+    p, o = pair(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    for _ in range(2):
+        p.step_sync(COND_ONLY, th, rv)
+        o.step_sync(COND_ONLY)
+    m3 = p.diag_moments(True, 0.0, 1.0, 3)
+    for wet in (True, False):
+        for edges in (np.geomspace(1e-9, 1e-3, 41), np.array([1e-9, 1.0]), np.geomspace(3e-8, 2e-6, 7)):
+            for k in range(4):
+                assert_close(f"spectrum wet={wet} k={k} bins={len(edges) - 1}", p.diag_spectrum(wet, edges, k),
+                             o.spectrum(wet, edges, k), atol=1e-300)
+    assert np.array_equal(sdm.sdm_outbuf(p.ctx), m3)
+    torch = pytest.importorskip("torch")
+    edges = np.geomspace(1e-9, 1e-3, 65)
+    out = torch.empty((64, p.n_cells), dtype=torch.float64, device="cuda")
+    sdm.sdm_diag_spectrum(p.ctx, True, edges, 3, out)
+    torch.cuda.synchronize()
+    assert_close("spectrum on device", out.cpu().numpy(), o.spectrum(True, edges, 3), atol=1e-300)
+    for bad in (np.array([1e-6, 1e-6]), np.array([1e-6, 1e-7]), np.geomspace(1e-9, 1e-3, 258)):
+        with pytest.raises(sdm.SdmError) as e:
+            p.diag_spectrum(True, bad, 0)
+        assert e.value.status == 1

@@ -106,3 +106,33 @@ def test_moments_brute_force():
                 np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-300)
     conc = o.sd_conc()
     assert conc.sum() == s.n and (conc == 16).all()
+
+
+def test_spectrum_matches_weighted_histogram():
+    """Binned spectrum: per cell, the bin of each radius from numpy's
+    digitize (half-open [e_b, e_b+1)) and bincount sums of N r^k (numpy's
+    weighted histogram differences cumulative sums, which loses digits),
+    divided by rho_d dV; a radius that
+    sits on an inner edge counts in the bin above it; the k = 0 spectrum
+    over bins that cover every radius sums to the concentration."""
+    w = workloads.icmw_2d(nx=3, nz=5, sd_conc=16, seed=7)
+    o = oracle.Oracle(w.cfg)
+    s = o.init(w.th, w.rv, w.rhod)
+    s.rw2[::3] *= 1e4
+    dV = 400.0
+    edges = np.geomspace(1e-9, 1e-3, 25)
+    s.rw2[5] = edges[7] ** 2  # exactly on an edge (sqrt of a square is exact)
+    cells = (s.x // 20.0).astype(int) * 5 + (s.z // 20.0).astype(int)
+    for wet in (True, False):
+        r = np.sqrt(s.rw2) if wet else np.cbrt(s.rd3)
+        for k in (0, 1, 3):
+            got = o.spectrum(wet, edges, k)
+            assert got.shape == (24, 15)
+            b = np.digitize(r, edges) - 1
+            for c in range(15):
+                sel = (cells == c) & (b >= 0) & (b < 24)
+                h = np.bincount(b[sel], weights=s.N[sel].astype(float) * r[sel] ** k, minlength=24)
+                np.testing.assert_allclose(got[:, c], h / (w.rhod.ravel()[c] * dV), rtol=1e-12, atol=1e-300)
+    got = o.spectrum(True, edges, 0)
+    assert got[7, cells[5]] > 0 and got[7, cells[5]] >= s.N[5] / (w.rhod.ravel()[cells[5]] * dV)
+    np.testing.assert_allclose(got.sum(axis=0), o.moments(True, 0.0, 1.0, 0), rtol=1e-12)
