@@ -57,7 +57,7 @@ class Opts(C.Structure):
     _fields_ = [
         ("adve", C.c_int), ("sedi", C.c_int), ("cond", C.c_int), ("coal", C.c_int),
         ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int),
-        ("coal_multi", C.c_int),
+        ("coal_multi", C.c_int), ("coal_adapt", C.c_int),
     ]
 
 
@@ -65,7 +65,7 @@ class Stats(C.Structure):
     _fields_ = [
         ("n_pairs", C.c_uint64), ("n_coll", C.c_uint64), ("n_pgt1", C.c_uint64),
         ("n_recycled", C.c_uint64), ("n_euler", C.c_uint64), ("n_bisect", C.c_uint64),
-        ("max_p", C.c_double), ("rainfall", C.c_double),
+        ("max_p", C.c_double), ("rainfall", C.c_double), ("n_coal_substeps", C.c_uint64),
     ]
 
     def as_dict(self):
@@ -176,7 +176,7 @@ def make_opts(o: dict | None = None) -> Opts:
     o = o or {}
     return Opts(o.get("adve", 1), o.get("sedi", 1), o.get("cond", 1), o.get("coal", 1),
                 o.get("RH_max", 44.0), o.get("sstp_cond", 10), o.get("sstp_coal", 10),
-                o.get("coal_multi", 0))
+                o.get("coal_multi", 0), o.get("coal_adapt", 0))
 
 
 def thermo(th, rv, rhod, RH_max=44.0) -> Thermo:

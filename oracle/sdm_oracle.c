@@ -679,7 +679,51 @@ static uint64_t n_events(double P, double u, uint64_t NL, uint64_t NS, int multi
     return g < cap ? g : cap;
 }
 
-/* sstp_coal substeps per cell.  In each: the cell's n super-droplets with
+/* Adaptive coalescence substeps (the paper plans to control the substep
+ * from P_ij, Sec. 5.1.4; READING): at the start of the step, per cell, an
+ * upper bound of eq. P_ij over every pair the cell's n super-droplets with
+ * N > 0 could form,
+ *   P_bound = N_max K_bound dt / dV * n (n-1) / (2 floor(n/2)),
+ * with K_bound = pi (2 r_max)^2 (v_max - v_min) for the geometric kernel
+ * (no pair has larger radii or a larger speed difference) and
+ * K_bound = b 2 V_max for Golovin's.  The cell takes
+ * max(sstp_coal, ceil(P_bound)) substeps, at most coal_adapt, so that no
+ * pair's P exceeds 1 at the first substep when the cap allows it. */
+static int adaptive_substeps(const orc_domain *d, const orc_opts *o, const orc_thermo *t,
+                             const orc_sds *s, const members *m, int64_t c, double dV)
+{
+    int64_t n = 0;
+    uint64_t Nmax = 0;
+    double rw2max = 0.0, vmax = 0.0, vmin = INFINITY;
+    for (int64_t q = m->start[c]; q < m->start[c + 1]; ++q) {
+        int64_t i = m->idx[q];
+        if (s->N[i] == 0) continue;
+        n++;
+        if (s->N[i] > Nmax) Nmax = s->N[i];
+        if (s->rw2[i] > rw2max) rw2max = s->rw2[i];
+        if (d->kernel != 1) {
+            double v = orc_vterm(s->rw2[i], t);
+            if (v > vmax) vmax = v;
+            if (v < vmin) vmin = v;
+        }
+    }
+    if (n < 2) return o->sstp_coal;
+    double rmax = sqrt(rw2max), K;
+    if (d->kernel == 1) {
+        K = d->golovin_b * (2.0 * (4.0 / 3.0 * PI * rw2max * rmax));
+    } else {
+        double two_r = 2.0 * rmax;
+        K = PI * two_r * two_r * (vmax - vmin);
+    }
+    double scale = (double)n * (double)(n - 1) / (2.0 * (double)(n / 2));
+    double Pb = (double)Nmax * K * d->dt / dV * scale;
+    int sstp = o->sstp_coal;
+    if (Pb > (double)sstp) sstp = Pb >= (double)o->coal_adapt ? o->coal_adapt : (int)ceil(Pb);
+    return sstp < o->sstp_coal ? o->sstp_coal : sstp;
+}
+
+/* sstp_coal substeps per cell (or the adaptive count above).  In each: the
+ * cell's n super-droplets with
  * non-zero multiplicity (READING: zero-multiplicity ones take no part) are
  * put in random order and paired (0,1), (2,3), ...; pair (i, j) collides
  * with probability (eq. P_ij)
@@ -695,12 +739,14 @@ void orc_coalesce(const orc_domain *d, const orc_opts *o, orc_sds *s, const doub
     members m = build_members(d, s);
     int64_t nc = orc_n_cells(d);
     double dV = cell_volume(d);
-    double dtpp = d->dt / o->sstp_coal;
     shuf *buf = malloc(sizeof(shuf) * (size_t)(s->n > 0 ? s->n : 1));
     for (int64_t c = 0; c < nc; ++c) {
         orc_thermo t;
         orc_thermo_eval(th[c], rv[c], rhod[c], 44.0, &t);
-        for (int sub = 0; sub < o->sstp_coal; ++sub) {
+        int sstp = o->coal_adapt > 0 ? adaptive_substeps(d, o, &t, s, &m, c, dV) : o->sstp_coal;
+        double dtpp = d->dt / sstp;
+        if (st) st->n_coal_substeps += (uint64_t)sstp;
+        for (int sub = 0; sub < sstp; ++sub) {
             int64_t n = 0;
             for (int64_t q = m.start[c]; q < m.start[c + 1]; ++q) {
                 int64_t i = m.idx[q];

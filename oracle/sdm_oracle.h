@@ -45,12 +45,14 @@ typedef struct {
     double RH_max;
     int sstp_cond, sstp_coal;
     int coal_multi;                /* 1: multiple coalescence for P_ij > 1      */
+    int coal_adapt;                /* > 0: adaptive coalescence substeps, at most this many */
 } orc_opts;
 
 typedef struct {
     uint64_t n_pairs, n_coll, n_pgt1, n_recycled, n_euler, n_bisect;
     double max_p;
     double rainfall;
+    uint64_t n_coal_substeps;      /* cell-substeps of coalescence taken        */
 } orc_stats;
 
 typedef struct {
