@@ -106,7 +106,7 @@ typedef struct {
     int cond_solver;
 } sdm_opts_init;
 
-/* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10, 0):
+/* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10, 0, 0):
  * process toggles, RH limit for drop growth, substep counts.
  * coal_multi = 0 is the paper's scheme: a pair with P_ij > 1 still has one
  * collision event (Sec. 5.1.4).  coal_multi = 1 turns on the multiple
@@ -114,12 +114,20 @@ typedef struct {
  * gamma = floor(P_ij) events, plus one when the pair's uniform number is
  * below P_ij - floor(P_ij), at most floor(N_L / N_S); the merged droplet
  * takes gamma droplets of the larger-multiplicity super-droplet.  Where
- * every P_ij <= 1 both give the same result bit for bit. */
+ * every P_ij <= 1 both give the same result bit for bit.
+ * coal_adapt > 0 turns on adaptive coalescence substeps, the substep control
+ * from P_ij that Sec. 5.1.4 also plans: per cell and step, from an upper
+ * bound of P_ij over every pair the cell could form at the start of the step
+ * (largest multiplicity, largest radius, terminal-velocity range),
+ * max(sstp_coal, ceil(P_bound)) substeps, at most coal_adapt.  0 keeps
+ * sstp_coal everywhere.  Single contexts only: sdm_ens_step returns
+ * SDM_EINVAL for coal_adapt > 0 (its substeps are one captured graph). */
 typedef struct {
     int adve, sedi, cond, coal;
     double RH_max;
     int sstp_cond, sstp_coal;
     int coal_multi;
+    int coal_adapt;
 } sdm_opts;
 
 /* Counters accumulated since sdm_init (or the last sdm_stats_reset). */
@@ -134,6 +142,9 @@ typedef struct {
     uint64_t n_zero;        /* multiplicity-zero super-droplets now            */
     double max_p;           /* largest P_ij seen                               */
     double rainfall;        /* liquid mass through the bottom [kg]              */
+    uint64_t n_coal_substeps; /* cell-substeps of coalescence taken (cells x
+                                 substeps summed over steps; single contexts,
+                                 0 for ensembles)                              */
 } sdm_stats;
 
 /* Per-phase device time [ms] accumulated while timing is on; measured with

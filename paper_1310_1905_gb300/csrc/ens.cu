@@ -869,13 +869,15 @@ sdm_status sdm_ens_members(const sdm_ens *e, int32_t *ids, int32_t cap, int32_t 
 // field by field: a caller's struct may carry any bytes in its padding
 static bool same_opts(const sdm_opts &a, const sdm_opts &b) {
     return a.adve == b.adve && a.sedi == b.sedi && a.cond == b.cond && a.coal == b.coal && a.RH_max == b.RH_max &&
-           a.sstp_cond == b.sstp_cond && a.sstp_coal == b.sstp_coal && a.coal_multi == b.coal_multi;
+           a.sstp_cond == b.sstp_cond && a.sstp_coal == b.sstp_coal && a.coal_multi == b.coal_multi &&
+           a.coal_adapt == b.coal_adapt;
 }
 
 sdm_status sdm_ens_step(sdm_ens *e, const sdm_opts *o, const int32_t *ids, const double *rhod, int32_t n) {
     if (!e || !o) return efail(e, SDM_EINVAL, "NULL argument");
     if (e->in_flight) return efail(e, SDM_ESTATE, "step before sdm_ens_wait of the previous one");
     if (o->sstp_cond < 1 || o->sstp_coal < 1) return efail(e, SDM_EINVAL, "substep counts must be >= 1");
+    if (o->coal_adapt != 0) return efail(e, SDM_EINVAL, "adaptive coalescence substeps: single contexts only");
     if (e->dirty_pack) {
         if (sdm_status s = pull_members(e)) return s;
         if (sdm_status s = repack(e, g_minit[e])) return s;

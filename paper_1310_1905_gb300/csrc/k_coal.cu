@@ -23,7 +23,7 @@ namespace sdm {
 
 struct CoalParams {
     Grid g;
-    int sstp, coal, kernel, mixed, multi;
+    int sstp, coal, kernel, mixed, multi, adapt;
     double golovin_b;
     uint64_t seed, step;
 };
@@ -156,6 +156,41 @@ __device__ __forceinline__ int collide(Acc &A, int a, int b, unsigned long long 
     return S;
 }
 
+// Adaptive substeps (coal_adapt > 0; the paper plans substep control from
+// P_ij, Sec. 5.1.4): from the cell's live count n, largest multiplicity,
+// largest r_w^2 and terminal-velocity range at the start of the step, an
+// upper bound of eq. P_ij over every pair the cell could form,
+//   P_bound = N_max K_bound dt / dV * n (n-1) / (2 floor(n/2)),
+// K_bound = pi (2 r_max)^2 (v_max - v_min) (geometric) or b 2 V_max
+// (Golovin); the cell takes max(sstp_coal, ceil(P_bound)) substeps, at most
+// coal_adapt.  Products only, so no contraction changes the rounding.
+__device__ __forceinline__ int adaptive_sstp(const CoalParams &p, int n, unsigned long long Nmax, double rw2max,
+                                             double vmax, double vmin) {
+    if (p.adapt <= 0 || n < 2) return p.sstp;
+    const double rmax = sqrt(rw2max);
+    double K;
+    if (p.kernel == SDM_KERNEL_GOLOVIN) {
+        K = p.golovin_b * (2.0 * (4.0 / 3.0 * phys::pi * rw2max * rmax));
+    } else {
+        const double two_r = 2.0 * rmax;
+        K = phys::pi * two_r * two_r * (vmax - vmin);
+    }
+    const double scale = (double)n * (double)(n - 1) / (2.0 * (double)(n / 2));
+    const double Pb = (double)Nmax * K * p.g.dt / p.g.dV * scale;
+    int s = p.sstp;
+    if (Pb > (double)s) s = Pb >= (double)p.adapt ? p.adapt : (int)ceil(Pb);
+    return s < p.sstp ? p.sstp : s;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
 // ---------------------------------------------------------------- warp path
 template <int CAP>
 struct WarpSmem {
@@ -235,10 +270,38 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     __syncwarp();
     unsigned long long n_pairs = 0, n_coll = 0, n_pgt1 = 0;
     double max_p = 0.0;
+    int sstp = p.sstp;
+    if (p.coal && p.adapt > 0) {
+        int nl = 0;
+        unsigned long long Nm = 0;
+        double rm = 0.0, vmax = 0.0, vmin = INFINITY;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = R * lane + r;
+            if (q < n && W.N[q] > 0) {
+                nl++;
+                Nm = W.N[q] > Nm ? W.N[q] : Nm;
+                rm = fmax(rm, W.rw2[q]);
+                if (geo) {
+                    vmax = fmax(vmax, W.vt[q]);
+                    vmin = fmin(vmin, W.vt[q]);
+                }
+            }
+        }
+        nl = (int)__reduce_add_sync(0xffffffffu, (unsigned)nl);
+        Nm = warp_max_u64(Nm);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+            vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            vmin = fmin(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        }
+        sstp = adaptive_sstp(p, nl, Nm, rm, vmax, vmin);
+    }
     if (p.coal && n >= 2) {
         SmemAcc<CAP> A{&W};
-        const double dtpp = p.g.dt / p.sstp;
-        for (int sub = 0; sub < p.sstp; ++sub) {
+        const double dtpp = p.g.dt / sstp;
+        for (int sub = 0; sub < sstp; ++sub) {
             int my_act = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -312,6 +375,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) max_p = fmax(max_p, __shfl_xor_sync(0xffffffffu, max_p, o));
     if (lane == 0) {
+        if (p.coal) atomicAdd(&st->n_coal_substeps, (unsigned long long)sstp);
         if (zeros) atomicAdd(&st->n_zero, (unsigned long long)zeros);
         if (np) atomicAdd(&st->n_pairs, (unsigned long long)np);
         if (nc) atomicAdd(&st->n_coll, (unsigned long long)nc);
@@ -367,6 +431,9 @@ __global__ void __launch_bounds__(kBigBlock)
     __shared__ int s_m;
     __shared__ unsigned long long s_cnt[4];
     __shared__ unsigned long long s_maxp;
+    __shared__ unsigned long long s_Nm[32];
+    __shared__ double s_rm[32], s_vmax[32], s_vmin[32];
+    __shared__ int s_n[32], s_sstp;
     const unsigned nbig = st->n_big;
     for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
         const int c = (int)bigcells[bi];
@@ -407,9 +474,57 @@ __global__ void __launch_bounds__(kBigBlock)
         const double nu = amb[2 * c], cX = amb[2 * c + 1];
         const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
         GlobalAcc A{dst, beg};
+        if (threadIdx.x == 0) s_sstp = p.sstp;
+        if (p.coal && p.adapt > 0) {  // adaptive_sstp from a block reduction
+            int nl = 0;
+            unsigned long long Nm = 0;
+            double rm = 0.0, vmax = 0.0, vmin = INFINITY;
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                const unsigned long long Nt = dst.N[beg + t];
+                if (Nt == 0) continue;
+                const double rw2 = dst.rw2[beg + t];
+                nl++;
+                Nm = Nt > Nm ? Nt : Nm;
+                rm = fmax(rm, rw2);
+                if (geo) {
+                    const double v = vt_of(p, rw2, sqrt(rw2), nu, cX);
+                    vmax = fmax(vmax, v);
+                    vmin = fmin(vmin, v);
+                }
+            }
+            nl = (int)__reduce_add_sync(0xffffffffu, (unsigned)nl);
+            Nm = warp_max_u64(Nm);
+            for (int o = 16; o > 0; o >>= 1) {
+                rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+                vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+                vmin = fmin(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+            }
+            const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            if ((threadIdx.x & 31) == 0) {
+                s_n[wid] = nl;
+                s_Nm[wid] = Nm;
+                s_rm[wid] = rm;
+                s_vmax[wid] = vmax;
+                s_vmin[wid] = vmin;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int k = 1; k < nw; ++k) {
+                    nl += s_n[k];
+                    Nm = s_Nm[k] > Nm ? s_Nm[k] : Nm;
+                    rm = fmax(rm, s_rm[k]);
+                    vmax = fmax(vmax, s_vmax[k]);
+                    vmin = fmin(vmin, s_vmin[k]);
+                }
+                s_sstp = adaptive_sstp(p, nl, Nm, rm, vmax, vmin);
+            }
+        }
+        __syncthreads();
+        const int sstp = s_sstp;
+        if (threadIdx.x == 0 && p.coal) atomicAdd(&st->n_coal_substeps, (unsigned long long)sstp);
         if (p.coal && n >= 2) {
-            const double dtpp = p.g.dt / p.sstp;
-            for (int sub = 0; sub < p.sstp; ++sub) {
+            const double dtpp = p.g.dt / sstp;
+            for (int sub = 0; sub < sstp; ++sub) {
                 if (threadIdx.x == 0) s_m = 0;
                 __syncthreads();
                 int my_m = 0;
@@ -483,6 +598,7 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     p.kernel = c->oi.kernel;
     p.mixed = c->oi.precision == SDM_PRECISION_MIXED;
     p.multi = o.coal_multi ? 1 : 0;
+    p.adapt = o.coal_adapt;
     p.golovin_b = c->oi.golovin_b;
     p.seed = c->oi.seed;
     p.step = c->step;

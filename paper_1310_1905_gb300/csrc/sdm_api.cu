@@ -294,6 +294,7 @@ sdm_status regroup(sdm_ctx *c) {
 sdm_status check_opts(sdm_ctx *c, const sdm_opts *o) {
     if (!o) return fail(c, SDM_EINVAL, "opts is NULL");
     if (o->sstp_cond < 1 || o->sstp_coal < 1) return fail(c, SDM_EINVAL, "substep counts must be >= 1");
+    if (o->coal_adapt < 0) return fail(c, SDM_EINVAL, "coal_adapt must be >= 0");
     if (!(o->RH_max > 0.0)) return fail(c, SDM_EINVAL, "RH_max must be positive");
     return SDM_OK;
 }
@@ -764,6 +765,7 @@ sdm_status sdm_get_stats(sdm_ctx *c, sdm_stats *out) {
     memcpy(&mp, &m.max_p_bits, sizeof(mp));
     out->max_p = mp;
     out->rainfall = m.rainfall;
+    out->n_coal_substeps = m.n_coal_substeps;
     return SDM_OK;
 }
 

@@ -251,6 +251,7 @@ struct DevStats {
     unsigned int flags;  // kFlag* bits
     unsigned int n_big;  // cells routed to the block coalescence path
     unsigned int n_rc_zero, n_rc_donor;
+    unsigned long long n_coal_substeps;  // cell-substeps of coalescence taken
 };
 enum : unsigned { kFlagNumeric = 1u, kFlagBigCell = 2u };
 

@@ -57,13 +57,13 @@ class sdm_opts_init(C.Structure):
 class sdm_opts(C.Structure):
     _fields_ = [("adve", C.c_int), ("sedi", C.c_int), ("cond", C.c_int), ("coal", C.c_int),
                 ("RH_max", C.c_double), ("sstp_cond", C.c_int), ("sstp_coal", C.c_int),
-                ("coal_multi", C.c_int)]
+                ("coal_multi", C.c_int), ("coal_adapt", C.c_int)]
 
 
 class sdm_stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("n_pairs", "n_coll", "n_pgt1", "n_recycled", "n_euler",
                                           "n_fallback", "n_steps", "n_zero")] + \
-               [("max_p", C.c_double), ("rainfall", C.c_double)]
+               [("max_p", C.c_double), ("rainfall", C.c_double), ("n_coal_substeps", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -178,7 +178,7 @@ def make_opts(d: dict | None = None) -> sdm_opts:
     d = d or {}
     return sdm_opts(d.get("adve", 1), d.get("sedi", 1), d.get("cond", 1), d.get("coal", 1),
                     d.get("RH_max", 44.0), d.get("sstp_cond", 10), d.get("sstp_coal", 10),
-                    d.get("coal_multi", 0))
+                    d.get("coal_multi", 0), d.get("coal_adapt", 0))
 
 
 def _check(L, ctx, status):
