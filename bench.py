@@ -40,11 +40,17 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (4 FP64 flops) per SM per clock
 FP64_FLOPS_PER_SM_CLK = 4.0
 N_SM = 152
-# ncu, k_condense on the 2D case (profiles/k_condense_icmw_2d_fp64.md):
-# FP64 flops the kernel executes (2 DFMA + DADD + DMUL) per SD-substep, and
-# DRAM bytes read + written per launch
-COND_FP64_FLOPS_PER_SD_SUBSTEP = 649.8
-COND_DRAM_BYTES_PER_LAUNCH = 11.81e6
+# ncu, k_condense in FP64: the FP64 flops it executes (2 DFMA + DADD + DMUL)
+# per SD-substep, and its DRAM bytes read + written per launch per
+# super-droplet, with the capture they come from
+# (profiles/k_condense_icmw_2d_fp64.md, profiles/kernels_updraft_3d_64cubed_fp64.md)
+COND_FP64 = {
+    "icmw_2d": dict(flops_per_sd_substep=649.8, dram_bytes_per_sd=11.81e6 / 360000,
+                    capture="2D case, 360 000 SDs, one launch"),
+    "updraft_3d": dict(flops_per_sd_substep=667.1, dram_bytes_per_sd=332.98e6 / 8388608,
+                       capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic scaled by the SDs of "
+                               "a launch (it grows in proportion: 39.7 B per SD against 40 B algorithmic)"),
+}
 
 
 def parse():
@@ -216,7 +222,7 @@ def run_gpu(args, rank: int, world: int):
         res["t_e2e"] = dist_max(t_e2e, world)
         nbytes = w.th.size * 8
         res["h2d"] = (2 * nbytes) if opts.get("cond", 1) else 0
-        res["d2h"] = (2 * nbytes if opts.get("cond", 1) else 0) + 128  # fields + the step's stats record
+        res["d2h"] = (2 * nbytes if opts.get("cond", 1) else 0) + 96  # fields + the 96-byte stats record of the wait
         q.close()
     p.close()
     return res
@@ -462,11 +468,12 @@ def main():
     sm_mhz = clk.get("sm_mhz") or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
     fp64_peak = FP64_FLOPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     units = res["n_sd"] * w.opts["sstp_cond"]
-    if args.precision == "fp64" and args.workload == "icmw_2d":
-        achieved = COND_FP64_FLOPS_PER_SD_SUBSTEP * units / (cond_ms * 1e-3) / 1e12
+    if args.precision == "fp64" and args.workload in COND_FP64:
+        k = COND_FP64[args.workload]
+        achieved = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
         roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
-                    frac=achieved / fp64_peak, traffic=COND_DRAM_BYTES_PER_LAUNCH,
-                    flops_per_sd_substep=COND_FP64_FLOPS_PER_SD_SUBSTEP,
+                    frac=achieved / fp64_peak, traffic=k["dram_bytes_per_sd"] * res["n_sd"],
+                    flops_per_sd_substep=k["flops_per_sd_substep"], counters=k["capture"],
                     peak_source="derived: 4 FP64 flop/SM/clk x 152 SMs x sampled SM clock (1.25 TFLOP/s nominal)")
     elif tim["cond_launches"] > 0:
         bytes_per_launch = 40.0 * res["n_sd"]

@@ -351,7 +351,7 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
         const uint32_t act = live[m];
         if ((j & 1u) == 0 && j + 1 < act) {
             const uint32_t a = val[q], b = val[q + 1];
-            const double scale = (double)act * (double)(act - 1) / (2.0 * (double)(act / 2));
+            const double scale = pair_scale(act);
             const double dtpp = p.dt / p.sstp;
             const double Ra = s.rw2[a], Rb = s.rw2[b];
             const unsigned long long Na = s.N[a], Nb = s.N[b];

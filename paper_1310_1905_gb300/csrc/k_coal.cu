@@ -88,8 +88,12 @@ __device__ __forceinline__ void warp_sort(KeyRec (&v)[R], int lane) {
     }
 }
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
-    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+// P_ij >= 0: its bit pattern orders like its value, so the statistics (the
+// count of P > 1 and the largest P) take integer operations, not FP64 ones
+constexpr unsigned long long kOneBits = 0x3FF0000000000000ull;  // 1.0
+
+__device__ __forceinline__ unsigned long long p_bits(double P) {
+    return (unsigned long long)__double_as_longlong(P);
 }
 
 // collection kernel: geometric (E = 1) or Golovin; ra = sqrt(rw2a), rb =
@@ -175,7 +179,7 @@ __device__ __forceinline__ int adaptive_sstp(const CoalParams &p, int n, unsigne
         const double two_r = 2.0 * rmax;
         K = phys::pi * two_r * two_r * (vmax - vmin);
     }
-    const double scale = (double)n * (double)(n - 1) / (2.0 * (double)(n / 2));
+    const double scale = pair_scale(n);
     const double Pb = (double)Nmax * K * p.g.dt / p.g.dV * scale;
     int s = p.sstp;
     if (Pb > (double)s) s = Pb >= (double)p.adapt ? p.adapt : (int)ceil(Pb);
@@ -216,8 +220,10 @@ struct SmemAcc {
     __device__ void setkappa(int i, double v) { w->kappa[i] = v; }
 };
 
-// cells of up to 32 R super-droplets, one warp each, R per lane
-template <int R>
+// cells of up to 32 R super-droplets, one warp each, R per lane.  EXT:
+// multiple coalescence or adaptive substeps on; the paper's scheme runs a
+// copy without their code.
+template <int R, bool EXT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_coal_warp(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
                 const double *amb, CoalParams p, uint32_t *bigcells, DevStats *st) {
@@ -268,10 +274,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
     }
     __syncwarp();
-    unsigned long long n_pairs = 0, n_coll = 0, n_pgt1 = 0;
-    double max_p = 0.0;
+    unsigned long long n_pairs = 0, n_coll = 0, n_pgt1 = 0, max_pb = 0;
     int sstp = p.sstp;
-    if (p.coal && p.adapt > 0) {
+    if (EXT && p.coal && p.adapt > 0) {
         int nl = 0;
         unsigned long long Nm = 0;
         double rm = 0.0, vmax = 0.0, vmin = INFINITY;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             __syncwarp();
             if (m < 2) continue;
             warp_sort<R>(v, lane);
-            const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
+            const double scale = pair_scale(m);
             // sorted positions R lane + r; pairs (2k, 2k + 1) are in one lane
             KeyRec pa[R >= 2 ? R / 2 : 1], pb[R >= 2 ? R / 2 : 1];
             if constexpr (R >= 2) {
@@ -343,9 +348,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     const double P = prob(p, Nmax, W.rw2[a], W.r[a], W.rw2[b], W.r[b], W.vt[a], W.vt[b], dtpp,
                                           scale);
                     n_pairs++;
-                    if (P > 1.0) n_pgt1++;
-                    max_p = fmax(max_p, P);
-                    const unsigned long long gam = n_events(P, W.acc[a], Nmax, Nmin, p.multi, p.mixed);
+                    const unsigned long long pb = p_bits(P);
+                    n_pgt1 += pb > kOneBits;
+                    max_pb = pb > max_pb ? pb : max_pb;
+                    const unsigned long long gam =
+                        n_events(P, W.acc[a], Nmax, Nmin, EXT ? p.multi : 0, p.mixed);
                     if (gam) {
                         const int S = collide(A, a, b, gam);
                         if (geo) W.vt[S] = vt_of(p, W.rw2[S], W.r[S], nu, cX);
@@ -372,15 +379,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)n_pairs);
     const unsigned nc = __reduce_add_sync(0xffffffffu, (unsigned)n_coll);
     const unsigned ng = __reduce_add_sync(0xffffffffu, (unsigned)n_pgt1);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) max_p = fmax(max_p, __shfl_xor_sync(0xffffffffu, max_p, o));
+    max_pb = warp_max_u64(max_pb);
     if (lane == 0) {
         if (p.coal) atomicAdd(&st->n_coal_substeps, (unsigned long long)sstp);
         if (zeros) atomicAdd(&st->n_zero, (unsigned long long)zeros);
         if (np) atomicAdd(&st->n_pairs, (unsigned long long)np);
         if (nc) atomicAdd(&st->n_coll, (unsigned long long)nc);
         if (ng) atomicAdd(&st->n_pgt1, (unsigned long long)ng);
-        if (max_p > 0.0) atomic_max_pos(&st->max_p_bits, max_p);
+        if (max_pb) atomicMax(&st->max_p_bits, max_pb);
     }
 }
 
@@ -549,9 +555,8 @@ __global__ void __launch_bounds__(kBigBlock)
                     continue;
                 }
                 block_sort(skey, spk, npow2);
-                const double scale = (double)m * (double)(m - 1) / (2.0 * (double)(m / 2));
-                unsigned long long np = 0, nc = 0, ng = 0;
-                double mp = 0.0;
+                const double scale = pair_scale(m);
+                unsigned long long np = 0, nc = 0, ng = 0, mpb = 0;
                 for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
                     const int a = (int)(spk[2 * k] & 0xffffffffu), b = (int)(spk[2 * k + 1] & 0xffffffffu);
                     const double rwa = A.rw2(a), rwb = A.rw2(b), ra = sqrt(rwa), rb = sqrt(rwb);
@@ -560,8 +565,9 @@ __global__ void __launch_bounds__(kBigBlock)
                     const double P = prob(p, Nmax, rwa, ra, rwb, rb, geo ? vt_of(p, rwa, ra, nu, cX) : 0.0,
                                           geo ? vt_of(p, rwb, rb, nu, cX) : 0.0, dtpp, scale);
                     np++;
-                    if (P > 1.0) ng++;
-                    mp = fmax(mp, P);
+                    const unsigned long long pb = p_bits(P);
+                    ng += pb > kOneBits;
+                    mpb = pb > mpb ? pb : mpb;
                     const unsigned long long gam = n_events(P, sacc[a], Nmax, Nmin, p.multi, p.mixed);
                     if (gam) {
                         collide(A, a, b, gam);
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(kBigBlock)
                 if (np) atomicAdd(&s_cnt[0], np);
                 if (nc) atomicAdd(&s_cnt[1], nc);
                 if (ng) atomicAdd(&s_cnt[2], ng);
-                if (mp > 0.0) atomicMax(&s_maxp, (unsigned long long)__double_as_longlong(mp));
+                if (mpb) atomicMax(&s_maxp, mpb);
                 __syncthreads();
             }
         }
@@ -610,15 +616,14 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     // records per lane: cells hold sd_conc on average and spread around it
     // as super-droplets move, so the warp path covers twice the mean
     const int per_cell = c->G * c->oi.sd_conc;
-    if (per_cell <= 16)
-        k_coal_warp<1><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
-                                                                  c->bigcells, c->dstats);
-    else if (per_cell <= 32)
-        k_coal_warp<2><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
-                                                                  c->bigcells, c->dstats);
-    else
-        k_coal_warp<4><<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
-                                                                  c->bigcells, c->dstats);
+    const bool ext = p.multi || p.adapt > 0;
+    auto launch = [&](auto kern) {
+        kern<<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p, c->bigcells,
+                                                        c->dstats);
+    };
+    if (per_cell <= 16) ext ? launch(k_coal_warp<1, true>) : launch(k_coal_warp<1, false>);
+    else if (per_cell <= 32) ext ? launch(k_coal_warp<2, true>) : launch(k_coal_warp<2, false>);
+    else ext ? launch(k_coal_warp<4, true>) : launch(k_coal_warp<4, false>);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(unsigned long long) * 3 * kBigCellCap;

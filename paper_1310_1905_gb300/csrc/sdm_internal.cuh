@@ -192,6 +192,13 @@ SDM_HD float vterm_f(float rw2, float nu, float cX) {
 // 24 random bits plus one half, times 2^-24: open (0,1) in FP32
 SDM_HD float u01f(uint64_t v) { return ((float)(uint32_t)(v >> 40) + 0.5f) * 5.9604645e-8f; }
 
+// The upscaling factor of eq. P_ij, n (n-1) / (2 floor(n/2)), is n - 1 for
+// even n and n for odd n.  Its FP64 evaluation from the formula is exact
+// for n < 2^26 (exact product, exact integer quotient), so this integer
+// form gives the same double while keeping the FP64 pipe free (on GB300 it
+// runs at 1/64 of the FP32 rate).
+SDM_HD double pair_scale(int64_t n) { return (double)((n & 1) ? n : n - 1); }
+
 // Collision events of a pair with scaled probability P (eq. P_ij), uniform
 // draw w and multiplicities NL >= NS > 0.  The paper's scheme (Sec. 5.1.4):
 // one event when u < P.  Multiple coalescence (multi = 1; Shima et al.
