@@ -226,7 +226,8 @@ sdm_status sdm_outbuf(sdm_ctx *ctx, double *dst, int dst_on_device);
  * over the super-droplets of cell c whose wet (wet = 1) or dry (wet = 0)
  * radius lies in [edges[b], edges[b+1]) (half-open: a radius falls in at
  * most one bin).  edges: host array of n_bins + 1 strictly increasing radii
- * [m]; 1 <= n_bins <= 256; 0 <= k <= 8 (SDM_EINVAL otherwise).  dst:
+ * [m], edges[0] >= 0; 1 <= n_bins <= 256; 0 <= k <= 8 (SDM_EINVAL
+ * otherwise).  dst:
  * n_bins * n_cells float64, bin-major, in host memory (dst_on_device = 0;
  * complete on return) or device memory (ordered on the context's stream).
  * Leaves the output buffer and the sdm_diag_rng selection untouched.  A
@@ -257,8 +258,12 @@ sdm_status sdm_sizes(const sdm_ctx *ctx, int64_t *n_sd, int64_t *n_cells);
 sdm_status sdm_get_attr(sdm_ctx *ctx, int attr, void *dst, int64_t n);
 
 /* Overwrite one attribute from host memory (storage order as returned by
- * sdm_get_attr).  Positions changed this way regroup the super-droplets
- * before the next step. */
+ * sdm_get_attr).  Positions changed this way regroup the super-droplets at
+ * the next step, diagnostic or sdm_get_attr, not before: a checkpoint
+ * (every attribute from sdm_get_attr, the step from sdm_get_step, theta and
+ * r_v) restores into any context of the same set-up through sdm_set_attr
+ * calls in any order and sdm_set_step, and the run then continues bit for
+ * bit as if uninterrupted. */
 sdm_status sdm_set_attr(sdm_ctx *ctx, int attr, const void *src, int64_t n);
 
 /* Copy the library's current theta and r_v (n_cells each) to host memory. */

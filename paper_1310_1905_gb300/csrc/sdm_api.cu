@@ -214,6 +214,8 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->outbuf);
     cudaFree(c->spec_buf);
     cudaFree(c->spec_edges);
+    cudaFree(c->cond_order);
+    cudaFree(c->cond_cost);
     for (int d = 0; d < 3; ++d) cudaFree(c->rhoC[d]);
     cudaFree(c->scan_tmp);
     cudaFree(c->rc_tmp);
@@ -640,6 +642,7 @@ sdm_status sdm_diag_spectrum(sdm_ctx *c, int wet, const double *edges, int n_bin
     if (!edges || !dst) return fail(c, SDM_EINVAL, "NULL argument");
     if (n_bins < 1 || n_bins > sdm::kMaxSpectrumBins) return fail(c, SDM_EINVAL, "n_bins must be 1..256");
     if (k < 0 || k > 8) return fail(c, SDM_EINVAL, "moment order must be 0..8");
+    if (!(edges[0] >= 0.0)) return fail(c, SDM_EINVAL, "bin edges are radii: edges[0] must be >= 0");
     for (int b = 0; b < n_bins; ++b)
         if (!(edges[b] < edges[b + 1])) return fail(c, SDM_EINVAL, "bin edges must increase strictly");
     if (c->layout_dirty)
@@ -716,8 +719,9 @@ sdm_status sdm_set_attr(sdm_ctx *c, int attr, const void *src, int64_t n) {
     if (!c || !src) return fail(c, SDM_EINVAL, "NULL argument");
     if (n != c->n_sd) return fail(c, SDM_EINVAL, "n must equal the number of super-droplets");
     if (c->async_in_flight) return fail(c, SDM_ESTATE, "set_attr while step_async is in flight");
-    if (c->layout_dirty)
-        if (sdm_status s = regroup(c)) return s;
+    // no regroup here even when positions were set: a restore writes every
+    // attribute in one storage order, and regrouping between two of its
+    // calls would permute the slots under it; the next use regroups
     size_t esz;
     void *p = attr_ptr(c, attr, &esz);
     if (!p) return fail(c, SDM_EINVAL, "unknown attribute or absent dimension");

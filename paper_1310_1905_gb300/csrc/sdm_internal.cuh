@@ -316,6 +316,10 @@ struct sdm_ctx {
     int diag_wet = 1;
     double diag_rmin = 0.0, diag_rmax = 0.0;
     double *spec_buf = nullptr, *spec_edges = nullptr;  // binned spectrum: n_bins x n_cells, n_bins + 1
+    uint32_t *cond_order = nullptr;                     // condensation: warps longest-first
+    float *cond_cost = nullptr;                         // and their cost in the last launch
+    int64_t cond_nw = 0;
+    bool cond_order_on = true;
     int spec_cap = 0;                                   // bins spec_buf holds
     uint64_t step = 0;
     uint64_t known_zeros = 0;

@@ -302,7 +302,8 @@ def test_spectrum_matches_oracle():
     sdm.sdm_diag_spectrum(p.ctx, True, edges, 3, out)
     torch.cuda.synchronize()
     assert_close("spectrum on device", out.cpu().numpy(), o.spectrum(True, edges, 3), atol=1e-300)
-    for bad in (np.array([1e-6, 1e-6]), np.array([1e-6, 1e-7]), np.geomspace(1e-9, 1e-3, 258)):
+    for bad in (np.array([1e-6, 1e-6]), np.array([1e-6, 1e-7]), np.geomspace(1e-9, 1e-3, 258),
+                np.array([-1e-6, 1e-6])):
         with pytest.raises(sdm.SdmError) as e:
             p.diag_spectrum(True, bad, 0)
         assert e.value.status == 1
