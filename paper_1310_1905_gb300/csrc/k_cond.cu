@@ -152,6 +152,7 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
 
 struct SolveCounters {
     int euler, fallback;
+    int evals;  // FP64 growth evaluations of the fast solve: the cost measure of the launch order
 };
 
 // The growth rate of eq. (maxmason) rearranged for FP64 throughput: with
@@ -629,6 +630,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     const int start = fs_start(S, tf, dtp, physics);
     for (int k = 0; k < 15; ++k) {
         const bool g0 = k == 0 && start != kStartPolish;
+        cnt.evals++;
         double mag;
         const double v = growth_eval(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
         if (g0) {
@@ -740,11 +742,19 @@ __device__ __noinline__ Thermo thermo_cond(double th, double rv, double rd, doub
     return thermo_eval_f<true>(th, rv, rd, RH_max, rdf);
 }
 
-template <int LPC, int MODE>
+// ORD: the warps take their work in order of decreasing cost (order),
+// which the previous launch recorded per warp into cost (its FP64 growth
+// evaluations, the bulk of a warp's time); see launch_condense_lpc.
+// Results do not depend on the order: cells are independent.
+template <int LPC, int MODE, bool ORD>
 __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32_t *offset, double *th, double *rv,
-                           const double *rhod, Grid g, int sstp, double RH_max, int physics, DevStats *st) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                           const double *rhod, Grid g, int sstp, double RH_max, int physics, DevStats *st,
+                           const uint32_t *order, float *cost, int64_t n_warps) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (ORD && wid >= n_warps) return;  // whole warps only: the kernel syncs within warps
+    const int64_t wmap = ORD ? (int64_t)order[wid] : wid;
     const int lane = threadIdx.x & 31;
+    const int64_t gt = wmap * 32 + lane;
     const int sl = lane % LPC;
     const int64_t c64 = gt / LPC;
     const bool live = c64 < g.n_cells;
@@ -753,7 +763,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     double thc = live ? th[c] : 289.0, rvc = live ? rv[c] : 0.0;
     const double rd = live ? rhod[c] : 1.0;
     const double dtp = g.dt / sstp;
-    SolveCounters cnt{0, 0};
+    SolveCounters cnt{0, 0, 0};
     bool bad = false;
     // the cell's ambient state for the solves sits in shared memory: read
     // there by reference it takes no registers across the solve
@@ -793,6 +803,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
     const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
     const unsigned anybad = __any_sync(0xffffffffu, bad);
+    const unsigned nev = ORD ? __reduce_add_sync(0xffffffffu, (unsigned)cnt.evals) : 0u;
     if (live && sl == 0) {
         th[c] = thc;
         rv[c] = rvc;
@@ -801,7 +812,44 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
         if (ne) atomicAdd(&st->n_euler, (unsigned long long)ne);
         if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
         if (anybad) atomicOr(&st->flags, kFlagNumeric);
+        if (ORD) cost[wmap] = (float)nev;
     }
+}
+
+// Longest work first: the warps' indices sorted by decreasing cost (ties by
+// index), one block, bitonic sort in shared memory of at most
+// kOrderMaxWarps keys (cost bits, inverted, above the index).
+constexpr int kOrderMaxWarps = 8192;
+
+__global__ void __launch_bounds__(1024) k_cond_order(const float *cost, uint32_t *order, int n) {
+    extern __shared__ unsigned long long s_key[];
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        if (i < n) {
+            const float cv = fmaxf(cost[i], 0.0f);  // non-negative: its bits order like its value
+            s_key[i] = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(cv)) << 32) | (unsigned)i;
+        } else {
+            s_key[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = s_key[i], b = s_key[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s_key[i] = b;
+                        s_key[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (uint32_t)(s_key[i] & 0xffffffffu);
 }
 
 // Ensemble condensation, one substep: a block per tile (tiles never straddle
@@ -824,7 +872,7 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
     const Thermo &t = s_t;
     const ThermoF &tf = s_tf;
     const double dtp = p.dt / p.sstp;
-    SolveCounters cnt{0, 0};
+    SolveCounters cnt{0, 0, 0};
     double sum = 0.0;
     bool bad = false;
     for (uint32_t i = tile_beg[tile] + threadIdx.x; i < tile_end[tile]; i += blockDim.x) {
@@ -883,12 +931,45 @@ cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t
     return cudaGetLastError();
 }
 
+// Where the launch is only a few waves of warps, the last wave decides the
+// time: one warp's solves take a sizeable part of the whole (2D case: about
+// 3 ms of 8).  There the warps run longest-first, in the order of their cost
+// in the previous launch (the cells change slowly from step to step); with
+// many waves (or no cost yet) the order is the cells' own.
 template <int LPC, int MODE>
 static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
     const int64_t threads = ((int64_t)c->grid.n_cells * LPC + 31) / 32 * 32;
-    k_condense<LPC, MODE><<<grid_for(threads, B), B, 0, c->stream>>>(
+    const int64_t n_warps = threads / 32;
+    if (LPC == 32 && c->cond_order_on && n_warps <= kOrderMaxWarps) {
+        if (c->cond_nw != n_warps) {
+            cudaFree(c->cond_order);
+            cudaFree(c->cond_cost);
+            c->cond_order = nullptr;
+            c->cond_cost = nullptr;
+            c->cond_nw = 0;
+            if (cudaMalloc(&c->cond_order, 4 * n_warps) == cudaSuccess &&
+                cudaMalloc(&c->cond_cost, 4 * n_warps) == cudaSuccess &&
+                cudaMemsetAsync(c->cond_cost, 0, 4 * n_warps, c->stream) == cudaSuccess)
+                c->cond_nw = n_warps;
+            cudaGetLastError();
+        }
+        if (c->cond_nw == n_warps) {
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_cond_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(8 * kOrderMaxWarps));
+                attr_set = true;
+            }
+            k_cond_order<<<1, 1024, 8 * kOrderMaxWarps, c->stream>>>(c->cond_cost, c->cond_order, (int)n_warps);
+            k_condense<LPC, MODE, LPC == 32><<<grid_for(threads, B), B, 0, c->stream>>>(
+                c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
+                c->dstats, c->cond_order, c->cond_cost, n_warps);
+            return;
+        }
+    }
+    k_condense<LPC, MODE, false><<<grid_for(threads, B), B, 0, c->stream>>>(
         c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
-        c->dstats);
+        c->dstats, nullptr, nullptr, n_warps);
 }
 
 template <int MODE>
