@@ -40,16 +40,23 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (4 FP64 flops) per SM per clock
 FP64_FLOPS_PER_SM_CLK = 4.0
 N_SM = 152
-# ncu, k_condense in FP64: the FP64 flops it executes (2 DFMA + DADD + DMUL)
-# per SD-substep, and its DRAM bytes read + written per launch per
-# super-droplet, with the capture they come from
-# (profiles/k_condense_icmw_2d_fp64.md, profiles/kernels_updraft_3d_64cubed_fp64.md)
+# ncu, k_condense: the FP64 flops it executes (2 DFMA + DADD + DMUL) per
+# SD-substep, its DRAM bytes read + written per launch per super-droplet and
+# the share of active cycles its FP64 pipe is busy, with the capture they
+# come from (profiles/k_condense_icmw_2d_fp64.md,
+# profiles/kernels_updraft_3d_64cubed_fp64.md).  Mixed precision too is
+# bound by its FP64 part (the solves near activation): its FP32 work is
+# about 1 % of the FP32 peak.
 COND_FP64 = {
-    "icmw_2d": dict(flops_per_sd_substep=649.8, dram_bytes_per_sd=11.81e6 / 360000,
-                    capture="2D case, 360 000 SDs, one launch"),
-    "updraft_3d": dict(flops_per_sd_substep=667.1, dram_bytes_per_sd=332.98e6 / 8388608,
-                       capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic scaled by the SDs of "
-                               "a launch (it grows in proportion: 39.7 B per SD against 40 B algorithmic)"),
+    ("icmw_2d", "fp64"): dict(flops_per_sd_substep=649.85, dram_bytes_per_sd=11.835e6 / 360000,
+                              fp64_pipe_active=0.7175, capture="2D case, 360 000 SDs, one launch"),
+    ("icmw_2d", "mixed"): dict(flops_per_sd_substep=181.44, dram_bytes_per_sd=12.361e6 / 360000,
+                               fp64_pipe_active=0.5925, capture="2D case, 360 000 SDs, one launch"),
+    ("updraft_3d", "fp64"): dict(flops_per_sd_substep=667.07, dram_bytes_per_sd=331.62e6 / 8388608,
+                                 fp64_pipe_active=0.7364,
+                                 capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic scaled by the "
+                                         "SDs of a launch (it grows in proportion: 39.5 B per SD against 40 B "
+                                         "algorithmic)"),
 }
 
 
@@ -468,12 +475,13 @@ def main():
     sm_mhz = clk.get("sm_mhz") or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
     fp64_peak = FP64_FLOPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     units = res["n_sd"] * w.opts["sstp_cond"]
-    if args.precision == "fp64" and args.workload in COND_FP64:
-        k = COND_FP64[args.workload]
+    if (args.workload, args.precision) in COND_FP64:
+        k = COND_FP64[(args.workload, args.precision)]
         achieved = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
         roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
                     frac=achieved / fp64_peak, traffic=k["dram_bytes_per_sd"] * res["n_sd"],
-                    flops_per_sd_substep=k["flops_per_sd_substep"], counters=k["capture"],
+                    flops_per_sd_substep=k["flops_per_sd_substep"], fp64_pipe_active=k["fp64_pipe_active"],
+                    counters=k["capture"],
                     peak_source="derived: 4 FP64 flop/SM/clk x 152 SMs x sampled SM clock (1.25 TFLOP/s nominal)")
     elif tim["cond_launches"] > 0:
         bytes_per_launch = 40.0 * res["n_sd"]

@@ -816,40 +816,56 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     }
 }
 
-// Longest work first: the warps' indices sorted by decreasing cost (ties by
-// index), one block, bitonic sort in shared memory of at most
-// kOrderMaxWarps keys (cost bits, inverted, above the index).
-constexpr int kOrderMaxWarps = 8192;
+// Longest work first: the warps' indices in order of decreasing cost, one
+// block.  A counting sort on 256 cost buckets spread linearly between the
+// smallest and the largest cost: the order within a bucket is whatever the
+// atomics give, which is harmless, since the order never changes a result.
+constexpr int kOrderMaxWarps = 8192, kOrderBuckets = 256;
 
 __global__ void __launch_bounds__(1024) k_cond_order(const float *cost, uint32_t *order, int n) {
-    extern __shared__ unsigned long long s_key[];
-    int np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-        if (i < n) {
-            const float cv = fmaxf(cost[i], 0.0f);  // non-negative: its bits order like its value
-            s_key[i] = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(cv)) << 32) | (unsigned)i;
-        } else {
-            s_key[i] = ~0ull;
+    __shared__ unsigned s_cnt[kOrderBuckets];
+    __shared__ float s_lo[32], s_hi[32];
+    float lo = INFINITY, hi = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float cv = fmaxf(cost[i], 0.0f);
+        lo = fminf(lo, cv);
+        hi = fmaxf(hi, cv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    lo = s_lo[0];
+    hi = s_hi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        lo = fminf(lo, s_lo[w]);
+        hi = fmaxf(hi, s_hi[w]);
+    }
+    const float scale = hi > lo ? (kOrderBuckets - 1) / (hi - lo) : 0.0f;
+    // bucket 0 holds the most expensive warps
+    auto bucket = [&](int i) {
+        const int b = (int)((hi - fmaxf(cost[i], 0.0f)) * scale);
+        return b < 0 ? 0 : (b >= kOrderBuckets ? kOrderBuckets - 1 : b);
+    };
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[bucket(i)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive scan of 256 counts
+        unsigned run = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            const unsigned c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
         }
     }
     __syncthreads();
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = s_key[i], b = s_key[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        s_key[i] = b;
-                        s_key[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (uint32_t)(s_key[i] & 0xffffffffu);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&s_cnt[bucket(i)], 1u)] = (uint32_t)i;
 }
 
 // Ensemble condensation, one substep: a block per tile (tiles never straddle
@@ -954,13 +970,7 @@ static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
             cudaGetLastError();
         }
         if (c->cond_nw == n_warps) {
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaFuncSetAttribute(k_cond_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(8 * kOrderMaxWarps));
-                attr_set = true;
-            }
-            k_cond_order<<<1, 1024, 8 * kOrderMaxWarps, c->stream>>>(c->cond_cost, c->cond_order, (int)n_warps);
+            k_cond_order<<<1, 1024, 0, c->stream>>>(c->cond_cost, c->cond_order, (int)n_warps);
             k_condense<LPC, MODE, LPC == 32><<<grid_for(threads, B), B, 0, c->stream>>>(
                 c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
                 c->dstats, c->cond_order, c->cond_cost, n_warps);
