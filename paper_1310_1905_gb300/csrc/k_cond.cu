@@ -769,6 +769,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     // there by reference it takes no registers across the solve
     __shared__ Thermo s_t[kMaxBlock / LPC];
     __shared__ ThermoF s_tf[kMaxBlock / LPC];
+    constexpr int kQueueCap = 128;  // FP64 queue of the mixed one-cell-per-warp solve
+    __shared__ uint32_t s_q[(MODE == kModeMixed && LPC == 32) ? kMaxBlock / 32 : 1][kQueueCap];
     const int gi = threadIdx.x / LPC;
     const Thermo &t = s_t[gi];
     const ThermoF &tf = s_tf[gi];
@@ -783,14 +785,65 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
         }
         __syncwarp();
         double sum = 0.0;
-        for (uint32_t i = beg + sl; i < end; i += LPC) {
-            const unsigned long long N = s.N[i];
-            if (N == 0) continue;
-            const double x0 = s.rw2[i];
-            const double x1 = solve_mode<MODE>(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
-            bad |= !isfinite(x1);
-            s.rw2[i] = x1;
-            sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+        if constexpr (MODE == kModeMixed && LPC == 32) {
+            // Mixed precision, one cell per warp: the FP32 solves first, in
+            // rounds of 32 super-droplets; those near activation are queued
+            // (in id order, by ballot) and then take the FP64 solve 32 at a
+            // time, so that its lanes are full instead of scattered
+            uint32_t *q = s_q[threadIdx.x >> 5];
+            int nq = 0;
+            for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                bool need64 = false;
+                unsigned long long N = 0;
+                if (i < end) N = s.N[i];
+                if (N != 0) {
+                    const double x0 = s.rw2[i], rd3 = s.rd3[i], kap = s.kappa[i];
+                    need64 = near_activation(x0, rd3, kap, t);
+                    if (!need64) {
+                        double x1;
+                        solve_rw2_f32(x0, rd3, kap, tf, (float)dtp, physics, &x1, cnt);
+                        bad |= !isfinite(x1);
+                        s.rw2[i] = x1;
+                        sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, need64);
+                if (need64) {
+                    const int pos = nq + __popc(m & ((1u << lane) - 1u));
+                    if (pos < kQueueCap) {
+                        q[pos] = i;
+                    } else {  // a cell far above its share: solve in place
+                        const double x0 = s.rw2[i];
+                        const double x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
+                        bad |= !isfinite(x1);
+                        s.rw2[i] = x1;
+                        sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+                    }
+                }
+                nq += __popc(m);
+            }
+            __syncwarp();
+            const int nqs = nq < kQueueCap ? nq : kQueueCap;
+            for (int k = lane; k < nqs; k += 32) {
+                const uint32_t i = q[k];
+                const unsigned long long N = s.N[i];
+                const double x0 = s.rw2[i];
+                const double x1 = solve_rw2_fast(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
+                bad |= !isfinite(x1);
+                s.rw2[i] = x1;
+                sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+            }
+        } else {
+            for (uint32_t i = beg + sl; i < end; i += LPC) {
+                const unsigned long long N = s.N[i];
+                if (N == 0) continue;
+                const double x0 = s.rw2[i];
+                const double x1 = solve_mode<MODE>(x0, s.rd3[i], s.kappa[i], t, tf, dtp, physics, cnt);
+                bad |= !isfinite(x1);
+                s.rw2[i] = x1;
+                sum += (double)N * (x1 * sqrt(x1) - x0 * sqrt(x0));
+            }
         }
 #pragma unroll
         for (int o = LPC / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
