@@ -50,8 +50,8 @@ N_SM = 152
 COND_FP64 = {
     ("icmw_2d", "fp64"): dict(flops_per_sd_substep=649.85, dram_bytes_per_sd=11.835e6 / 360000,
                               fp64_pipe_active=0.7175, capture="2D case, 360 000 SDs, one launch"),
-    ("icmw_2d", "mixed"): dict(flops_per_sd_substep=181.44, dram_bytes_per_sd=12.361e6 / 360000,
-                               fp64_pipe_active=0.5925, capture="2D case, 360 000 SDs, one launch"),
+    ("icmw_2d", "mixed"): dict(flops_per_sd_substep=178.07, dram_bytes_per_sd=11.895e6 / 360000,
+                               fp64_pipe_active=0.5272, capture="2D case, 360 000 SDs, one launch"),
     ("updraft_3d", "fp64"): dict(flops_per_sd_substep=667.07, dram_bytes_per_sd=331.62e6 / 8388608,
                                  fp64_pipe_active=0.7364,
                                  capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic scaled by the "
