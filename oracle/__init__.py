@@ -126,6 +126,8 @@ def lib():
             L.orc_moments.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _D, _D, C.c_int, _P(_D)]
             L.orc_spectrum.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _P(_D), C.c_int, C.c_int, _P(_D)]
             L.orc_sd_conc.argtypes = [_P(Domain), _P(SDs), _P(_D)]
+            L.orc_upwind.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), _P(_D), _P(_D)]
+            L.orc_relax.argtypes = [_P(Domain), _P(_D), _P(_D), _D, _D]
             _lib = L
     return _lib
 
@@ -303,11 +305,41 @@ class Oracle:
         lib().orc_spectrum(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), _dp(edges), nb, k, _dp(out))
         return out.reshape(nb, self.n_cells)
 
+    def euler_step(self, rhoCx=None, rhoCy=None, rhoCz=None, th0=None, rv0=None, tau_rlx=300.0, z_rlx=200.0):
+        """The Eulerian component on theta and r_v: a donor-cell step, then
+        (with th0, rv0 profiles) the relaxation of the horizontal means."""
+        self.th = upwind(self.cfg, self.th, self.rhod, rhoCx, rhoCy, rhoCz)
+        self.rv = upwind(self.cfg, self.rv, self.rhod, rhoCx, rhoCy, rhoCz)
+        if th0 is not None:
+            self.th = relax(self.cfg, self.th, th0, tau_rlx, z_rlx)
+            self.rv = relax(self.cfg, self.rv, rv0, tau_rlx, z_rlx)
+
     def sd_conc(self):
         out = np.zeros(self.n_cells)
         s = self.state.struct()
         lib().orc_sd_conc(C.byref(self.dom), C.byref(s), _dp(out))
         return out
+
+
+def _field(a):
+    return None if a is None else np.ascontiguousarray(a, np.float64).ravel()
+
+
+def upwind(cfg: dict, psi, rhod, rhoCx=None, rhoCy=None, rhoCz=None):
+    """One donor-cell step of the cell field psi (a new flat array)."""
+    dom = make_domain(cfg)
+    out = np.ascontiguousarray(psi, np.float64).ravel().copy()
+    lib().orc_upwind(C.byref(dom), _dp(out), _dp(_field(rhod)), _dp(_field(rhoCx)), _dp(_field(rhoCy)),
+                     _dp(_field(rhoCz)))
+    return out
+
+
+def relax(cfg: dict, psi, psi0, tau_rlx=300.0, z_rlx=200.0):
+    """Relaxation of the horizontal means toward psi0 (nz values), one step."""
+    dom = make_domain(cfg)
+    out = np.ascontiguousarray(psi, np.float64).ravel().copy()
+    lib().orc_relax(C.byref(dom), _dp(out), _dp(np.ascontiguousarray(psi0, np.float64)), tau_rlx, z_rlx)
+    return out
 
 
 def solve_rw2(x0, rd3, kappa, t: Thermo, dtp, physics=1):

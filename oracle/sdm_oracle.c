@@ -842,6 +842,76 @@ void orc_spectrum(const orc_domain *d, const orc_sds *s, const double *rhod, int
         for (int64_t c = 0; c < nc; ++c) out[b * nc + c] /= rhod[c] * dV;
 }
 
+/* ---- Eulerian component of the kinematic framework (Sec. 2.1-2.2) ----------
+ * The paper transports theta and r_v with MPDATA (libmpdata++), outside the
+ * particle scheme.  READING: a first-order donor-cell (upwind) scheme stands
+ * in for it, in flux form with the same rho_d C Courant fields the particles
+ * use (edge arrays of the Arakawa-C grid):
+ *   rho_d psi' = rho_d psi - sum over the cell's edges of the outward
+ *                (rho_d C)_edge psi_up,
+ * psi_up the value in the cell the flow comes from.  Periodic in x and y;
+ * on a z boundary edge the value is the inside cell's (zero gradient).
+ * rho_d is stationary (Sec. 2.1: the flow is divergence free in the rho_d
+ * weighted sense), so psi' = (rho_d psi') / rho_d. */
+static double up_flux(double C, double left, double right) { return C * (C >= 0.0 ? left : right); }
+
+void orc_upwind(const orc_domain *d, double *psi, const double *rhod, const double *rhoCx,
+                const double *rhoCy, const double *rhoCz)
+{
+    int64_t NX = dimn(d->nx), NY = dimn(d->ny), NZ = dimn(d->nz), nc = NX * NY * NZ;
+    double *old = malloc(sizeof(double) * (size_t)nc);
+    for (int64_t c = 0; c < nc; ++c) old[c] = psi[c];
+    for (int64_t i = 0; i < NX; ++i)
+        for (int64_t j = 0; j < NY; ++j)
+            for (int64_t k = 0; k < NZ; ++k) {
+                int64_t c = (i * NY + j) * NZ + k;
+                double out = 0.0;  /* net outward flux of rho_d psi */
+                if (d->nx > 0 && rhoCx) {
+                    int64_t il = (i - 1 + NX) % NX, ir = (i + 1) % NX;
+                    double Cl = rhoCx[(i * NY + j) * NZ + k], Cr = rhoCx[((i + 1) * NY + j) * NZ + k];
+                    out += up_flux(Cr, old[c], old[(ir * NY + j) * NZ + k]);
+                    out -= up_flux(Cl, old[(il * NY + j) * NZ + k], old[c]);
+                }
+                if (d->ny > 0 && rhoCy) {
+                    int64_t jl = (j - 1 + NY) % NY, jr = (j + 1) % NY;
+                    double Cl = rhoCy[(i * (NY + 1) + j) * NZ + k], Cr = rhoCy[(i * (NY + 1) + j + 1) * NZ + k];
+                    out += up_flux(Cr, old[c], old[(i * NY + jr) * NZ + k]);
+                    out -= up_flux(Cl, old[(i * NY + jl) * NZ + k], old[c]);
+                }
+                if (d->nz > 0 && rhoCz) {
+                    double below = k > 0 ? old[c - 1] : old[c], above = k < NZ - 1 ? old[c + 1] : old[c];
+                    double Cb = rhoCz[(i * NY + j) * (NZ + 1) + k], Ct = rhoCz[(i * NY + j) * (NZ + 1) + k + 1];
+                    out += up_flux(Ct, old[c], above);
+                    out -= up_flux(Cb, below, old[c]);
+                }
+                psi[c] = (rhod[c] * old[c] - out) / rhod[c];
+            }
+    free(old);
+}
+
+/* Relaxation of the horizontal means (Sec. 2.2): at every level the mean
+ * <psi> over x (and y) moves toward the initial profile psi0 by
+ *   dt (psi0 - <psi>) / tau,  tau = tau_rlx exp(z / z_rlx),
+ * z at the level's cell centres, added to every cell of the level (explicit
+ * Euler).  READING: the printed source term carries the opposite sign,
+ * which would drive the mean away from the initial profile the text says it
+ * is relaxed to. */
+void orc_relax(const orc_domain *d, double *psi, const double *psi0, double tau_rlx, double z_rlx)
+{
+    int64_t NX = dimn(d->nx), NY = dimn(d->ny), NZ = dimn(d->nz);
+    for (int64_t k = 0; k < NZ; ++k) {
+        double sum = 0.0;
+        for (int64_t i = 0; i < NX; ++i)
+            for (int64_t j = 0; j < NY; ++j) sum += psi[(i * NY + j) * NZ + k];
+        double mean = sum / (double)(NX * NY);
+        double z = (k + 0.5) * d->dz;
+        double tau = tau_rlx * exp(z / z_rlx);
+        double inc = d->dt * (psi0[k] - mean) / tau;
+        for (int64_t i = 0; i < NX; ++i)
+            for (int64_t j = 0; j < NY; ++j) psi[(i * NY + j) * NZ + k] += inc;
+    }
+}
+
 /* READING: super-droplet "concentration" is the count of super-droplets with
  * non-zero multiplicity in each cell. */
 void orc_sd_conc(const orc_domain *d, const orc_sds *s, double *out)

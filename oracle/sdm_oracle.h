@@ -108,6 +108,9 @@ void orc_step_async(const orc_domain *d, const orc_opts *o, orc_sds *s, const do
 void orc_moments(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
                  double r_min, double r_max, int k, double *out);
 void orc_sd_conc(const orc_domain *d, const orc_sds *s, double *out);
+void orc_upwind(const orc_domain *d, double *psi, const double *rhod, const double *rhoCx,
+                const double *rhoCy, const double *rhoCz);
+void orc_relax(const orc_domain *d, double *psi, const double *psi0, double tau_rlx, double z_rlx);
 void orc_spectrum(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
                   const double *edges, int n_bins, int k, double *out);
 
