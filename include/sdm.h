@@ -148,10 +148,15 @@ typedef struct {
 } sdm_stats;
 
 /* Per-phase device time [ms] accumulated while timing is on; measured with
- * CUDA events on the context's stream around each group of launches. */
+ * CUDA events on the context's stream around each group of launches.
+ * launches counts the particle scheme's kernels (steps and diagnostics);
+ * euler_ms and euler_launches the Eulerian stand-in (sdm_euler_step), which
+ * is the driver's part, apart. */
 typedef struct {
     double cond_ms, recycle_ms, move_ms, sort_ms, coal_ms, diag_ms, copy_ms;
     uint64_t cond_launches, coal_launches, launches;
+    double euler_ms;
+    uint64_t euler_launches;
 } sdm_timing;
 
 /* ---- life cycle --------------------------------------------------------- */
@@ -200,6 +205,35 @@ sdm_status sdm_step_async(sdm_ctx *ctx, const sdm_opts *opts);
  * rainfall_out (nullable) receives the accumulated rainfall [kg] (the paper's
  * step_async return value).  SDM_ETIMEOUT leaves the work in flight. */
 sdm_status sdm_wait(sdm_ctx *ctx, double timeout_s, double *rainfall_out);
+
+/* ---- the kinematic framework's Eulerian component (Sec. 2.1-2.2) --------
+ * Not part of the particle scheme: the paper's driver transports theta and
+ * r_v with MPDATA (libmpdata++).  This stand-in lets a driver of this
+ * library run the ICMW set-up on the device:
+ *   advect: one first-order donor-cell (upwind) step of theta and r_v in
+ *     flux form with the same rho_d C Courant fields (Arakawa-C edge arrays,
+ *     as for sdm_step_sync): rho_d psi' = rho_d psi - sum over the cell's
+ *     edges of the outward (rho_d C)_edge psi_up, psi_up taken in the cell
+ *     the flow comes from; periodic in x and y, a z boundary edge takes the
+ *     inside cell's value; rho_d is stationary (Sec. 2.1);
+ *   relax: then each level's horizontal mean moves toward the initial
+ *     profile, psi += dt (psi0 - <psi>) / tau, tau = tau_rlx exp(z / z_rlx),
+ *     z at the level's cell centres (Sec. 2.2: 300 s and 200 m).
+ * th0, rv0: host arrays of nz values (nz = 1 without a z dimension). */
+typedef struct {
+    int advect, relax;
+    double tau_rlx, z_rlx;
+    const double *th0, *rv0;
+} sdm_euler_opts;
+
+/* One Eulerian step on the caller's theta and r_v (host or device arrays,
+ * overwritten; complete on return for host arrays, ordered on the context's
+ * stream for device ones).  SDM_ESTATE while step_async is in flight;
+ * SDM_EINVAL for missing fields, or relaxation without profiles or with a
+ * non-positive time or height scale.  Allocates two small device buffers on
+ * its first call. */
+sdm_status sdm_euler_step(sdm_ctx *ctx, const sdm_euler_opts *opts, sdm_arr th, sdm_arr rv, sdm_arr rhoCx,
+                          sdm_arr rhoCy, sdm_arr rhoCz);
 
 /* ---- diagnostics (Sec. 5.2.1, diag_* and outbuf) ------------------------ */
 

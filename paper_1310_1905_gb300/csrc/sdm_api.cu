@@ -216,6 +216,8 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->spec_edges);
     cudaFree(c->cond_order);
     cudaFree(c->cond_cost);
+    cudaFree(c->euler_tmp);
+    cudaFree(c->euler_prof);
     for (int d = 0; d < 3; ++d) cudaFree(c->rhoC[d]);
     cudaFree(c->scan_tmp);
     cudaFree(c->rc_tmp);
@@ -232,7 +234,7 @@ void free_ctx(sdm_ctx *c) {
     delete c;
 }
 
-enum { PH_COND, PH_RECYCLE, PH_MOVE, PH_SORT, PH_COAL, PH_DIAG, PH_COPY };
+enum { PH_COND, PH_RECYCLE, PH_MOVE, PH_SORT, PH_COAL, PH_DIAG, PH_COPY, PH_EULER };
 
 cudaEvent_t pool_event(sdm_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -494,6 +496,76 @@ sdm_status sdm_destroy(sdm_ctx *c) {
     return SDM_OK;
 }
 
+// the caller's rho_d C fields into the context's edge arrays (allocated on
+// first use); absent arrays and absent dimensions are skipped
+static sdm_status courant_in(sdm_ctx *c, const sdm_arr &rhoCx, const sdm_arr &rhoCy, const sdm_arr &rhoCz) {
+    const sdm_arr *C[3] = {&rhoCx, &rhoCy, &rhoCz};
+    const int dims[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
+    for (int d = 0; d < 3; ++d) {
+        if (!C[d]->data_zero || dims[d] == 0) continue;
+        if (!c->rhoC[d]) {
+            int shape[3];
+            const int nd = field_shape(c, d, shape);
+            int64_t tot = 1;
+            for (int q = 0; q < nd; ++q) tot *= shape[q];
+            CK(cudaMalloc(&c->rhoC[d], tot * 8), "Courant allocation");
+        }
+        if (sdm_status s = field_in(c, c->rhoC[d], *C[d], d, "rhoC")) return s;
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_euler_step(sdm_ctx *c, const sdm_euler_opts *o, sdm_arr th, sdm_arr rv, sdm_arr rhoCx,
+                          sdm_arr rhoCy, sdm_arr rhoCz) {
+    if (!c || !o) return fail(c, SDM_EINVAL, "NULL argument");
+    if (c->async_in_flight) return fail(c, SDM_ESTATE, "euler_step called before sdm_wait of step_async");
+    if (!th.data_zero || !rv.data_zero) return fail(c, SDM_EINVAL, "th and rv are required");
+    if (o->relax && (!o->th0 || !o->rv0 || !(o->tau_rlx > 0.0) || !(o->z_rlx > 0.0)))
+        return fail(c, SDM_EINVAL, "relaxation needs th0, rv0 and positive tau_rlx, z_rlx");
+    const int nz = c->grid.NZ;
+    if (!c->euler_tmp) CK(cudaMalloc(&c->euler_tmp, 8 * (size_t)c->grid.n_cells), "Eulerian scratch");
+    if (!c->euler_prof) CK(cudaMalloc(&c->euler_prof, 16 * (size_t)nz), "Eulerian scratch");
+    Phase ph(c, PH_EULER);
+    struct EulerCount {  // the field copies' launches count as the Eulerian step's too
+        sdm_ctx *c;
+        uint64_t l0;
+        ~EulerCount() {
+            c->tacc.euler_launches += c->tacc.launches - l0;
+            c->tacc.launches = l0;
+        }
+    } count_guard{c, c->tacc.launches};
+    if (sdm_status s = field_in(c, c->th, th, -1, "th")) return s;
+    if (sdm_status s = field_in(c, c->rv, rv, -1, "rv")) return s;
+    if (o->advect)
+        if (sdm_status s = courant_in(c, rhoCx, rhoCy, rhoCz)) return s;
+    if (o->relax) {
+        CK(cudaMemcpyAsync(c->euler_prof, o->th0, 8 * (size_t)nz, cudaMemcpyHostToDevice, c->stream), "profiles");
+        CK(cudaMemcpyAsync(c->euler_prof + nz, o->rv0, 8 * (size_t)nz, cudaMemcpyHostToDevice, c->stream),
+           "profiles");
+    }
+    double *f[2] = {c->th, c->rv};
+    for (int q = 0; q < 2; ++q) {
+        if (o->advect) {
+            CK(cudaMemcpyAsync(c->euler_tmp, f[q], 8 * (size_t)c->grid.n_cells, cudaMemcpyDeviceToDevice,
+                               c->stream),
+               "Eulerian copy");
+            CK(launch_upwind(c->euler_tmp, f[q], c->rhod, rhoCx.data_zero ? c->rhoC[0] : nullptr,
+                             rhoCy.data_zero ? c->rhoC[1] : nullptr, rhoCz.data_zero ? c->rhoC[2] : nullptr,
+                             c->grid, c->stream),
+               "upwind");
+            c->tacc.launches += 1;
+        }
+        if (o->relax) {
+            CK(launch_relax(f[q], c->euler_prof + q * nz, c->grid, o->tau_rlx, o->z_rlx, c->stream), "relax");
+            c->tacc.launches += 1;
+        }
+    }
+    if (sdm_status s = field_out(c, th, c->th, "th")) return s;
+    if (sdm_status s = field_out(c, rv, c->rv, "rv")) return s;
+    if (!th.on_device || !rv.on_device) CK(cudaStreamSynchronize(c->stream), "euler_step");
+    return SDM_OK;
+}
+
 sdm_status sdm_step_sync(sdm_ctx *c, const sdm_opts *o, sdm_arr th, sdm_arr rv, sdm_arr rhoCx,
                          sdm_arr rhoCy, sdm_arr rhoCz, sdm_arr rhod) {
     if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
@@ -506,19 +578,7 @@ sdm_status sdm_step_sync(sdm_ctx *c, const sdm_opts *o, sdm_arr th, sdm_arr rv, 
         if (sdm_status s = field_in(c, c->rv, rv, -1, "rv")) return s;
         if (rhod.data_zero)
             if (sdm_status s = field_in(c, c->rhod, rhod, -1, "rhod")) return s;
-        const sdm_arr *C[3] = {&rhoCx, &rhoCy, &rhoCz};
-        const int dims[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
-        for (int d = 0; d < 3; ++d) {
-            if (!C[d]->data_zero || dims[d] == 0) continue;
-            if (!c->rhoC[d]) {
-                int shape[3];
-                const int nd = field_shape(c, d, shape);
-                int64_t tot = 1;
-                for (int q = 0; q < nd; ++q) tot *= shape[q];
-                CK(cudaMalloc(&c->rhoC[d], tot * 8), "Courant allocation");
-            }
-            if (sdm_status s = field_in(c, c->rhoC[d], *C[d], d, "rhoC")) return s;
-        }
+        if (sdm_status s = courant_in(c, rhoCx, rhoCy, rhoCz)) return s;
     }
     if (c->layout_dirty)
         if (sdm_status s = regroup(c)) return s;
@@ -793,6 +853,7 @@ sdm_status sdm_get_timing(sdm_ctx *c, sdm_timing *out, int reset) {
             case PH_SORT: dst = &c->tacc.sort_ms; break;
             case PH_COAL: dst = &c->tacc.coal_ms; break;
             case PH_DIAG: dst = &c->tacc.diag_ms; break;
+            case PH_EULER: dst = &c->tacc.euler_ms; break;
             default: dst = &c->tacc.copy_ms; break;
         }
         *dst += ms;

@@ -320,6 +320,7 @@ struct sdm_ctx {
     float *cond_cost = nullptr;                         // and their cost in the last launch
     int64_t cond_nw = 0;
     bool cond_order_on = true;
+    double *euler_tmp = nullptr, *euler_prof = nullptr;  // Eulerian stand-in: old field, th0 and rv0 profiles
     int spec_cap = 0;                                   // bins spec_buf holds
     uint64_t step = 0;
     uint64_t known_zeros = 0;
@@ -345,6 +346,10 @@ cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
 cudaError_t launch_moments(sdm_ctx *c, int k);
 cudaError_t launch_sd_conc(sdm_ctx *c);
 constexpr int kMaxSpectrumBins = 256;
+cudaError_t launch_upwind(const double *old, double *out, const double *rhod, const double *Cx, const double *Cy,
+                          const double *Cz, const Grid &g, cudaStream_t st);
+cudaError_t launch_relax(double *psi, const double *psi0, const Grid &g, double tau_rlx, double z_rlx,
+                         cudaStream_t st);
 cudaError_t launch_spectrum(sdm_ctx *c, int wet, int n_bins, int k);
 cudaError_t launch_field_gather(double *dst, const double *src, const int64_t *strides, int ndim,
                                 const int *shape, cudaStream_t s);

@@ -60,6 +60,11 @@ class sdm_opts(C.Structure):
                 ("coal_multi", C.c_int), ("coal_adapt", C.c_int)]
 
 
+class sdm_euler_opts(C.Structure):
+    _fields_ = [("advect", C.c_int), ("relax", C.c_int), ("tau_rlx", C.c_double), ("z_rlx", C.c_double),
+                ("th0", C.POINTER(C.c_double)), ("rv0", C.POINTER(C.c_double))]
+
+
 class sdm_stats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("n_pairs", "n_coll", "n_pgt1", "n_recycled", "n_euler",
                                           "n_fallback", "n_steps", "n_zero")] + \
@@ -72,13 +77,15 @@ class sdm_stats(C.Structure):
 class sdm_timing(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("cond_ms", "recycle_ms", "move_ms", "sort_ms", "coal_ms",
                                           "diag_ms", "copy_ms")] + \
-               [(k, C.c_uint64) for k in ("cond_launches", "coal_launches", "launches")]
+               [(k, C.c_uint64) for k in ("cond_launches", "coal_launches", "launches")] + \
+               [("euler_ms", C.c_double), ("euler_launches", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_step_async", "sdm_wait",
+           "sdm_euler_step",
            "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
            "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc"]
@@ -104,6 +111,7 @@ def load(build_if_missing: bool = True):
     L.sdm_init.argtypes = [P(sdm_opts_init), sdm_arr, sdm_arr, sdm_arr, sdm_arr, sdm_arr, sdm_arr, V, P(ctx)]
     L.sdm_destroy.argtypes = [ctx]
     L.sdm_step_sync.argtypes = [ctx, P(sdm_opts), sdm_arr, sdm_arr, sdm_arr, sdm_arr, sdm_arr, sdm_arr]
+    L.sdm_euler_step.argtypes = [ctx, P(sdm_euler_opts), sdm_arr, sdm_arr, sdm_arr, sdm_arr, sdm_arr]
     L.sdm_step_async.argtypes = [ctx, P(sdm_opts)]
     L.sdm_wait.argtypes = [ctx, D, P(D)]
     L.sdm_diag_rng.argtypes = [ctx, C.c_int, D, D]
@@ -208,6 +216,21 @@ def sdm_step_sync(ctx, opts: dict, th, rv, rhoCx=None, rhoCy=None, rhoCz=None, r
     o = make_opts(opts)
     args = [_Arr(a) for a in (th, rv, rhoCx, rhoCy, rhoCz, rhod)]
     _check(L, ctx, L.sdm_step_sync(ctx, C.byref(o), *[a.c for a in args]))
+
+
+def sdm_euler_step(ctx, th, rv, rhoCx=None, rhoCy=None, rhoCz=None, th0=None, rv0=None, advect=True,
+                   tau_rlx=300.0, z_rlx=200.0):
+    """The kinematic framework's Eulerian step on theta and r_v (in place):
+    donor-cell transport, then (with th0, rv0 level profiles) relaxation of
+    the horizontal means."""
+    L = load()
+    relax = th0 is not None
+    p0 = np.ascontiguousarray(th0 if relax else [0.0], np.float64)
+    p1 = np.ascontiguousarray(rv0 if relax else [0.0], np.float64)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    o = sdm_euler_opts(int(advect), int(relax), tau_rlx, z_rlx, dp(p0), dp(p1))
+    args = [_Arr(a) for a in (th, rv, rhoCx, rhoCy, rhoCz)]
+    _check(L, ctx, L.sdm_euler_step(ctx, C.byref(o), *[a.c for a in args]))
 
 
 def sdm_step_async(ctx, opts: dict):
@@ -367,6 +390,9 @@ class Particles:
 
     def step_async(self, opts):
         sdm_step_async(self.ctx, opts)
+
+    def euler_step(self, th, rv, rhoCx=None, rhoCy=None, rhoCz=None, th0=None, rv0=None, advect=True):
+        sdm_euler_step(self.ctx, th, rv, rhoCx, rhoCy, rhoCz, th0, rv0, advect)
 
     def wait(self, timeout_s=-1.0):
         return sdm_wait(self.ctx, timeout_s)
