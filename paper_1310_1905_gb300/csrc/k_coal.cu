@@ -627,12 +627,9 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(unsigned long long) * 3 * kBigCellCap;
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_coal_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    e = smem_attr_once(k_coal_block, (int)smem, attr_done);
+    if (e != cudaSuccess) return e;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     int blocks = nsm > 0 ? nsm : 152;

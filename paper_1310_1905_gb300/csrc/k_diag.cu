@@ -182,13 +182,9 @@ size_t spectrum_smem_bytes(int n_bins) {
 
 cudaError_t launch_spectrum(sdm_ctx *c, int wet, int n_bins, int k) {
     const size_t smem = spectrum_smem_bytes(n_bins);
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)spectrum_smem_bytes(kMaxSpectrumBins));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    const cudaError_t e = smem_attr_once(k_spectrum, (int)spectrum_smem_bytes(kMaxSpectrumBins), attr_done);
+    if (e != cudaSuccess) return e;
     const int nb = (c->grid.n_cells + kDiagCells - 1) / kDiagCells;
     k_spectrum<<<nb, kDiagWarps * 32, smem, c->stream>>>(c->buf[c->cur], c->offset, c->rhod, c->grid, c->spec_edges,
                                                          n_bins, wet, k, c->spec_buf);

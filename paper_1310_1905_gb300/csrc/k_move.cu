@@ -63,17 +63,59 @@ __device__ __forceinline__ double advect_1d(double x, double h, int i, double Cl
     return (x + h * (Cl - (double)i * dC)) / (1.0 - dC);
 }
 
+// periodic wrap into [0, X): w = fmod(x, X), plus X if negative, 0 if that
+// rounds to X.  Within one period of the domain (every Courant number below
+// 1) the same value comes from a comparison and at most one exact
+// subtraction or one rounded addition: FP64 fmod is a loop of FP64 work.
 __device__ __forceinline__ double wrap(double x, double X) {
+    if (x >= 0.0 && x < X) return x;
+    if (x > -X && x < 0.0) {  // fmod returns x itself
+        const double w = x + X;
+        return w >= X ? 0.0 : w;
+    }
+    if (x >= X && x < 2.0 * X) return x - X;  // exact: X <= x <= 2X
     double w = fmod(x, X);
     if (w < 0.0) w += X;
     if (w >= X) w = 0.0;
     return w;
 }
 
+// The Courant number of every edge, C = (rho_d C) / rho_d,edge (courant_x,
+// _y, _z), once per step: the super-droplets of a cell share its edges, so
+// k_move reads them instead of dividing per super-droplet.  The same
+// operations on the same operands: the values are those courant_* give.
+__global__ void k_courant(Grid g, const double *rhod, const double *Cx, const double *Cy, const double *Cz,
+                          double *Ex, double *Ey, double *Ez) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (Cx) {
+        const int64_t n = (int64_t)(g.nx + 1) * g.NY * g.NZ;
+        if (t < n) {
+            const int ie = (int)(t / ((int64_t)g.NY * g.NZ)), j = (int)((t / g.NZ) % g.NY), k = (int)(t % g.NZ);
+            Ex[t] = courant_x(g, rhod, Cx, ie, j, k);
+        }
+    }
+    if (Cy) {
+        const int64_t n = (int64_t)g.NX * (g.ny + 1) * g.NZ;
+        if (t < n) {
+            const int i = (int)(t / ((int64_t)(g.ny + 1) * g.NZ)), je = (int)((t / g.NZ) % (g.ny + 1));
+            const int k = (int)(t % g.NZ);
+            Ey[t] = courant_y(g, rhod, Cy, i, je, k);
+        }
+    }
+    if (Cz) {
+        const int64_t n = (int64_t)g.NX * g.NY * (g.nz + 1);
+        if (t < n) {
+            const int i = (int)(t / ((int64_t)g.NY * (g.nz + 1))), j = (int)((t / (g.nz + 1)) % g.NY);
+            const int ke = (int)(t % (g.nz + 1));
+            Ez[t] = courant_z(g, rhod, Cz, i, j, ke);
+        }
+    }
+}
+
 struct MoveParams {
     Grid g;
     int adve, sedi, transport, mixed;
-    const double *Cx, *Cy, *Cz;
+    const double *Cx, *Cy, *Cz;  // Courant numbers of the edges (k_courant)
 };
 
 __global__ void k_move(SdArrays s, int64_t n, MoveParams p, const double *rhod, const double *amb,
@@ -92,16 +134,16 @@ __global__ void k_move(SdArrays s, int64_t n, MoveParams p, const double *rhod, 
                          : vterm(s.rw2[q], amb[2 * c], amb[2 * c + 1]);
         if (p.adve) {
             if (g.nx > 0 && p.Cx)
-                x = wrap(advect_1d(x, g.dx, i, courant_x(g, rhod, p.Cx, i, j, k),
-                                   courant_x(g, rhod, p.Cx, i + 1, j, k)),
+                x = wrap(advect_1d(x, g.dx, i, p.Cx[((int64_t)i * g.NY + j) * g.NZ + k],
+                                   p.Cx[((int64_t)(i + 1) * g.NY + j) * g.NZ + k]),
                          g.nx * g.dx);
             if (g.ny > 0 && p.Cy)
-                y = wrap(advect_1d(y, g.dy, j, courant_y(g, rhod, p.Cy, i, j, k),
-                                   courant_y(g, rhod, p.Cy, i, j + 1, k)),
+                y = wrap(advect_1d(y, g.dy, j, p.Cy[((int64_t)i * (g.NY + 1) + j) * g.NZ + k],
+                                   p.Cy[((int64_t)i * (g.NY + 1) + j + 1) * g.NZ + k]),
                          g.ny * g.dy);
             if (g.nz > 0 && p.Cz)
-                z = advect_1d(z, g.dz, k, courant_z(g, rhod, p.Cz, i, j, k),
-                              courant_z(g, rhod, p.Cz, i, j, k + 1));
+                z = advect_1d(z, g.dz, k, p.Cz[((int64_t)i * g.NY + j) * (g.NZ + 1) + k],
+                              p.Cz[((int64_t)i * g.NY + j) * (g.NZ + 1) + k + 1]);
         }
         if (p.transport && g.nz > 0) {
             const double Z = g.nz * g.dz;
@@ -136,12 +178,30 @@ cudaError_t launch_move(sdm_ctx *c, const sdm_opts &o) {
     p.sedi = o.sedi;
     p.mixed = c->oi.precision == SDM_PRECISION_MIXED;
     p.transport = o.adve || o.sedi;
-    p.Cx = c->rhoC[0];
-    p.Cy = c->rhoC[1];
-    p.Cz = c->rhoC[2];
-    cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * (c->grid.n_cells + 1), c->stream);
-    if (e != cudaSuccess) return e;
+    p.Cx = p.Cy = p.Cz = nullptr;
     const int B = 256;
+    cudaError_t e;
+    if (o.adve && (c->rhoC[0] || c->rhoC[1] || c->rhoC[2])) {
+        const Grid &g = c->grid;
+        const int64_t ne[3] = {(int64_t)(g.nx + 1) * g.NY * g.NZ, (int64_t)g.NX * (g.ny + 1) * g.NZ,
+                               (int64_t)g.NX * g.NY * (g.nz + 1)};
+        int64_t nmax = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (!c->rhoC[d]) continue;
+            if (!c->cedge[d]) {
+                e = cudaMalloc(&c->cedge[d], 8 * (size_t)ne[d]);
+                if (e != cudaSuccess) return e;
+            }
+            nmax = ne[d] > nmax ? ne[d] : nmax;
+        }
+        k_courant<<<grid_for(nmax, B), B, 0, c->stream>>>(g, c->rhod, c->rhoC[0], c->rhoC[1], c->rhoC[2], c->cedge[0],
+                                                          c->cedge[1], c->cedge[2]);
+        p.Cx = c->rhoC[0] ? c->cedge[0] : nullptr;
+        p.Cy = c->rhoC[1] ? c->cedge[1] : nullptr;
+        p.Cz = c->rhoC[2] ? c->cedge[2] : nullptr;
+    }
+    e = cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * (c->grid.n_cells + 1), c->stream);
+    if (e != cudaSuccess) return e;
     k_move<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->buf[c->cur], c->n_sd, p, c->rhod, c->amb,
                                                        c->count, c->newcell, c->slot, c->dstats);
     return cudaGetLastError();

@@ -225,14 +225,9 @@ cudaError_t sort_records(SortRec *rec, uint32_t n, uint32_t npow2, cudaStream_t 
     const int B = 256;
     if (npow2 > n) k_fill_max<<<grid_for(npow2 - n, B), B, 0, st>>>(rec, n, npow2);
     if (npow2 <= (uint32_t)kSmemSort) {
-        static bool attr_set = false;
-        const int bytes = (int)(sizeof(SortRec) * kSmemSort);
-        if (!attr_set) {
-            const cudaError_t e =
-                cudaFuncSetAttribute(k_sort_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static std::atomic<unsigned long long> attr_done{0};
+        const cudaError_t e = smem_attr_once(k_sort_smem, (int)(sizeof(SortRec) * kSmemSort), attr_done);
+        if (e != cudaSuccess) return e;
         k_sort_smem<<<1, 1024, sizeof(SortRec) * npow2, st>>>(rec, npow2);
         return cudaGetLastError();
     }

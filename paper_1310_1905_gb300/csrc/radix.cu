@@ -134,13 +134,8 @@ static size_t staged_smem() {
 
 template <class K, class P>
 static cudaError_t staged_attr() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_rs_scatter_staged<K, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)staged_smem<K, P>());
-    done = e == cudaSuccess;
-    return e;
+    static std::atomic<unsigned long long> done{0};
+    return smem_attr_once(k_rs_scatter_staged<K, P>, (int)staged_smem<K, P>(), done);
 }
 
 // Sort n records by (aux, key) where aux < 2^(8*aux_bytes) and only the

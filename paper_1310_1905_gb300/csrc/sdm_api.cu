@@ -9,6 +9,8 @@
 #include <chrono>
 #include <thread>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sdm_internal.cuh"
 
 using namespace sdm;
@@ -218,6 +220,7 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->cond_cost);
     cudaFree(c->euler_tmp);
     cudaFree(c->euler_prof);
+    for (int d = 0; d < 3; ++d) cudaFree(c->cedge[d]);
     for (int d = 0; d < 3; ++d) cudaFree(c->rhoC[d]);
     cudaFree(c->scan_tmp);
     cudaFree(c->rc_tmp);
@@ -235,6 +238,10 @@ void free_ctx(sdm_ctx *c) {
 }
 
 enum { PH_COND, PH_RECYCLE, PH_MOVE, PH_SORT, PH_COAL, PH_DIAG, PH_COPY, PH_EULER };
+// NVTX range names of the phases (a profiler's timeline shows them; without
+// one attached the calls cost next to nothing)
+static const char *const kPhaseName[] = {"sdm condensation", "sdm recycling", "sdm transport",  "sdm sort",
+                                         "sdm coalescence",  "sdm diagnostics", "sdm field copies", "sdm eulerian"};
 
 cudaEvent_t pool_event(sdm_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -252,12 +259,14 @@ struct Phase {  // records a CUDA-event pair around a group of launches
     int ph;
     cudaEvent_t a = nullptr;
     Phase(sdm_ctx *c_, int ph_) : c(c_), ph(ph_) {
+        nvtxRangePushA(kPhaseName[ph_]);
         if (c->timing) {
             a = pool_event(c);
             cudaEventRecord(a, c->stream);
         }
     }
     ~Phase() {
+        nvtxRangePop();
         if (c->timing && a) {
             cudaEvent_t b = pool_event(c);
             cudaEventRecord(b, c->stream);
@@ -622,7 +631,7 @@ sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
         Phase ph(c, PH_MOVE);
         CK(launch_ambient(c), "ambient");
         CK(launch_move(c, *o), "move");
-        c->tacc.launches += 2;
+        c->tacc.launches += 2 + (o->adve && (c->rhoC[0] || c->rhoC[1] || c->rhoC[2]) ? 1 : 0);  // + k_courant
     }
     {
         Phase ph(c, PH_SORT);

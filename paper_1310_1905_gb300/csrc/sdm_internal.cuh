@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -321,6 +322,7 @@ struct sdm_ctx {
     int64_t cond_nw = 0;
     bool cond_order_on = true;
     double *euler_tmp = nullptr, *euler_prof = nullptr;  // Eulerian stand-in: old field, th0 and rv0 profiles
+    double *cedge[3] = {nullptr, nullptr, nullptr};       // Courant numbers of the edges, per step
     int spec_cap = 0;                                   // bins spec_buf holds
     uint64_t step = 0;
     uint64_t known_zeros = 0;
@@ -402,6 +404,21 @@ void sdm_set_global_error(const std::string &msg);
 // ensemble members): the outermost ln r where n(ln r) dlnr dV >= 1
 bool rd_range_modes(const std::vector<sdm_lognormal> &modes, double kap, int64_t sd_conc, double dV,
                     double *lo_out, double *hi_out);
+
+// A kernel's dynamic shared-memory limit, raised once per device (the
+// attribute belongs to each device's copy of the function): done holds one
+// bit per device id below 64; devices beyond set it on every call.
+template <class F>
+inline cudaError_t smem_attr_once(F *kern, int bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load() & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit);
+    return e;
+}
 
 inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)((n + block - 1) / block);
