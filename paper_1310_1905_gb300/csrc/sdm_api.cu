@@ -4,6 +4,7 @@
 // in the kernels of this directory; host code only moves arguments.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -183,10 +184,18 @@ bool sdm::rd_range_modes(const std::vector<sdm_lognormal> &modes, double kap, in
 
 namespace {
 
+// Fault injection on the host, for tests of the allocation-failure path
+// without a GPU fault: with SDM_FAIL_ALLOC=k in the environment, the k-th
+// device allocation of each sdm_init reports cudaErrorMemoryAllocation
+// instead of allocating (sdm_init then returns SDM_ENOMEM and frees what it
+// had).  Read at every sdm_init; unset, it costs one getenv per init.
+static thread_local int g_fail_alloc = 0;
+
 template <class T>
 cudaError_t dalloc(T **p, size_t n) {
     *p = nullptr;
     if (n == 0) return cudaSuccess;
+    if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;  // injected
     return cudaMalloc((void **)p, n * sizeof(T));
 }
 
@@ -325,6 +334,10 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
                     sdm_arr rhoCy, sdm_arr rhoCz, void *stream, sdm_ctx **out) {
     if (!oi || !out) return fail(nullptr, SDM_EINVAL, "opts and out must not be NULL");
     *out = nullptr;
+    {
+        const char *fa = getenv("SDM_FAIL_ALLOC");
+        g_fail_alloc = fa ? atoi(fa) : 0;
+    }
     if (oi->backend != SDM_BACKEND_CUDA)
         return fail(nullptr, SDM_EINVAL, "only the CUDA back-end exists (no CPU fallback)");
     if (oi->nx < 0 || oi->ny < 0 || oi->nz < 0) return fail(nullptr, SDM_EINVAL, "negative cell count");
@@ -494,6 +507,7 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
         free_ctx(c);
         return fail(nullptr, st, msg);
     }
+    g_fail_alloc = 0;
     *out = c;
     return SDM_OK;
 }

@@ -75,3 +75,25 @@ def test_non_finite_radius_reported():
     with pytest.raises(sdm.SdmError) as e:
         p.step_sync(dict(ALL, adve=0, sedi=0, coal=0), th, rv)
     assert e.value.status == 5  # SDM_ENUMERIC
+
+
+def test_injected_allocation_failure_reports_enomem(monkeypatch):
+    """SDM_FAIL_ALLOC=k makes the k-th device allocation of sdm_init fail on
+    the host: the call returns SDM_ENOMEM, frees what it had taken, and a
+    later init succeeds."""
+    torch = pytest.importorskip("torch")
+    w = workloads.icmw_2d(nx=4, nz=5, sd_conc=8, seed=3)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 3, 9, 17, 25):
+        monkeypatch.setenv("SDM_FAIL_ALLOC", str(k))
+        with pytest.raises(sdm.SdmError) as e:
+            gpu_particles(w)
+        assert e.value.status == 2  # SDM_ENOMEM
+    monkeypatch.delenv("SDM_FAIL_ALLOC")
+    p = gpu_particles(w)
+    th, rv = w.th.copy(), w.rv.copy()
+    p.step_sync(ALL, th, rv)
+    p.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)  # nothing left behind
