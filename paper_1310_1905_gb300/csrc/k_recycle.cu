@@ -117,6 +117,80 @@ __global__ void k_rc_apply(SdArrays s, const SortRec *zrec, const SortRec *drec,
     s.N[d] = Nd - Nd / 2;
 }
 
+// records ordered by (hi, lo), ties by val
+__device__ __forceinline__ bool srec_gt(const SortRec &a, const SortRec &b) {
+    return a.hi > b.hi || (a.hi == b.hi && (a.lo > b.lo || (a.lo == b.lo && a.val > b.val)));
+}
+
+// The whole recycling in one block where the state has at most kSmemSort
+// super-droplets: zeros and donors go into one shared-memory array keyed so
+// that one bitonic sort puts the zeros first, by id (key: the id, below
+// 2^32), then the donors by (N descending, id ascending) (key: ~N, which
+// for any multiplicity below 2^63 lies above every id), and the k-th zero
+// takes the k-th donor.  No count travels to the host in between.
+__global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *st) {
+    extern __shared__ SortRec r[];
+    __shared__ unsigned s_m, s_nz;
+    if (threadIdx.x == 0) s_m = s_nz = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long N = s.N[i];
+        if (N == 0) {
+            r[atomicAdd(&s_m, 1u)] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
+            atomicAdd(&s_nz, 1u);
+        } else if (N >= 2) {
+            r[atomicAdd(&s_m, 1u)] = SortRec{~N, s.uid[i], (uint32_t)i};
+        }
+    }
+    __syncthreads();
+    const unsigned m = s_m, nz = s_nz, nd = m - nz;
+    unsigned np2 = 1;
+    while (np2 < m) np2 <<= 1;
+    for (unsigned i = m + threadIdx.x; i < np2; i += blockDim.x) r[i] = SortRec{~0ull, ~0u, ~0u};
+    __syncthreads();
+    for (unsigned k = 2; k <= np2; k <<= 1) {
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned i = threadIdx.x; i < np2; i += blockDim.x) {
+                const unsigned ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const SortRec a = r[i], b = r[ixj];
+                    if (srec_gt(a, b) == up) {
+                        r[i] = b;
+                        r[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned np = nz < nd ? nz : nd;
+    for (unsigned q = threadIdx.x; q < np; q += blockDim.x) {
+        const uint32_t z = r[q].val, d = r[nz + q].val;
+        s.rw2[z] = s.rw2[d];
+        s.rd3[z] = s.rd3[d];
+        s.kappa[z] = s.kappa[d];
+        if (s.x) s.x[z] = s.x[d];
+        if (s.y) s.y[z] = s.y[d];
+        if (s.z) s.z[z] = s.z[d];
+        const unsigned long long Nd = s.N[d];
+        s.N[z] = Nd / 2;
+        s.N[d] = Nd - Nd / 2;
+    }
+    if (threadIdx.x == 0 && np) atomicAdd(&st->n_recycled, (unsigned long long)np);
+}
+
+bool recycle_small(const sdm_ctx *c) { return c->n_sd <= kSmemSort; }
+
+cudaError_t launch_recycle_small(sdm_ctx *c) {
+    static std::atomic<unsigned long long> attr_done{0};
+    const int bytes = (int)(sizeof(SortRec) * kSmemSort);
+    cudaError_t e = smem_attr_once(k_rc_small, bytes, attr_done);
+    if (e != cudaSuccess) return e;
+    k_rc_small<<<1, 1024, bytes, c->stream>>>(c->buf[c->cur], (int)c->n_sd, c->dstats);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_recycle_compact(sdm_ctx *c) {
     cudaError_t e = cudaMemsetAsync(&c->dstats->n_rc_zero, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
@@ -174,9 +248,6 @@ cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd) {
 }
 
 // ---- bitonic sort of SortRec records by (hi, lo), padded to a power of two
-__device__ __forceinline__ bool srec_gt(const SortRec &a, const SortRec &b) {
-    return a.hi > b.hi || (a.hi == b.hi && (a.lo > b.lo || (a.lo == b.lo && a.val > b.val)));
-}
 
 __global__ void k_fill_max(SortRec *r, uint32_t from, uint32_t to) {
     const uint32_t i = from + blockIdx.x * blockDim.x + threadIdx.x;

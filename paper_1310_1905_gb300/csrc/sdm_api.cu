@@ -631,7 +631,11 @@ sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
     if (c->async_in_flight) return fail(c, SDM_ESTATE, "step_async called twice without sdm_wait");
     if (c->layout_dirty)
         if (sdm_status s = regroup(c)) return s;
-    if (c->known_zeros > 0) {
+    if (c->known_zeros > 0 && recycle_small(c)) {  // one block, no count through the host
+        Phase ph(c, PH_RECYCLE);
+        CK(launch_recycle_small(c), "recycle");
+        c->tacc.launches += 1;
+    } else if (c->known_zeros > 0) {
         Phase ph(c, PH_RECYCLE);
         CK(launch_recycle_compact(c), "recycle compact");
         c->tacc.launches += 1;
@@ -843,7 +847,7 @@ sdm_status sdm_get_stats(sdm_ctx *c, sdm_stats *out) {
     out->n_pairs = m.n_pairs;
     out->n_coll = m.n_coll;
     out->n_pgt1 = m.n_pgt1;
-    out->n_recycled = c->host_recycled;
+    out->n_recycled = c->host_recycled + m.n_recycled;  // the large path counts on the host, the small on the device
     out->n_euler = m.n_euler;
     out->n_fallback = m.n_fallback;
     out->n_steps = c->step;

@@ -344,6 +344,8 @@ cudaError_t launch_move(sdm_ctx *c, const sdm_opts &o);
 cudaError_t launch_regroup(sdm_ctx *c);  // scan + perm (after move)
 cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal);
 cudaError_t launch_recycle_compact(sdm_ctx *c);
+bool recycle_small(const sdm_ctx *c);
+cudaError_t launch_recycle_small(sdm_ctx *c);
 cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
 cudaError_t launch_moments(sdm_ctx *c, int k);
 cudaError_t launch_sd_conc(sdm_ctx *c);
