@@ -123,15 +123,25 @@ __device__ __forceinline__ bool srec_gt(const SortRec &a, const SortRec &b) {
 }
 
 // The whole recycling in one block where the state has at most kSmemSort
-// super-droplets: zeros and donors go into one shared-memory array keyed so
-// that one bitonic sort puts the zeros first, by id (key: the id, below
-// 2^32), then the donors by (N descending, id ascending) (key: ~N, which
-// for any multiplicity below 2^63 lies above every id), and the k-th zero
-// takes the k-th donor.  No count travels to the host in between.
+// super-droplets, with no count travelling to the host.  The zeros are
+// compacted (key: the id).  Of the donors only the first np = min(zeros,
+// donors) in (N descending, id ascending) order are needed: a radix select
+// over the key (~N, id), eight 8-bit digits of ~N from the top and then
+// four of the id, finds the np-th smallest key T, and the donors with keys
+// up to T are appended (key: ~N, which for any multiplicity below 2^63 lies
+// above every id).  One bitonic sort of the zeros and those donors puts the
+// zeros first, by id, then the donors in order; the k-th zero takes the
+// k-th donor.
 __global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *st) {
     extern __shared__ SortRec r[];
-    __shared__ unsigned s_m, s_nz;
-    if (threadIdx.x == 0) s_m = s_nz = 0;
+    __shared__ unsigned s_m, s_nz, s_nd, s_k, hist[256];
+    __shared__ unsigned long long s_phi, s_mhi;  // fixed digits of ~N and their mask
+    __shared__ unsigned s_plo, s_mlo;            // fixed digits of the id and their mask
+    if (threadIdx.x == 0) {
+        s_m = s_nz = s_nd = 0;
+        s_phi = s_mhi = 0ull;
+        s_plo = s_mlo = 0u;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long N = s.N[i];
@@ -139,11 +149,75 @@ __global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *
             r[atomicAdd(&s_m, 1u)] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
             atomicAdd(&s_nz, 1u);
         } else if (N >= 2) {
-            r[atomicAdd(&s_m, 1u)] = SortRec{~N, s.uid[i], (uint32_t)i};
+            atomicAdd(&s_nd, 1u);
         }
     }
     __syncthreads();
-    const unsigned m = s_m, nz = s_nz, nd = m - nz;
+    const unsigned nz = s_nz, nd = s_nd, np = nz < nd ? nz : nd;
+    if (np == 0) return;
+    const bool take_all = nd <= nz;
+    if (!take_all) {
+        if (threadIdx.x == 0) s_k = np;  // the rank (from 1) still to find under the fixed digits
+        for (int pass = 0; pass < 12; ++pass) {
+            const bool on_id = pass >= 8;
+            const int shift = on_id ? 24 - 8 * (pass - 8) : 56 - 8 * pass;
+            if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+            __syncthreads();
+            const unsigned long long phi = s_phi, mhi = s_mhi;
+            const unsigned plo = s_plo, mlo = s_mlo;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const unsigned long long N = s.N[i];
+                if (N < 2) continue;
+                const unsigned long long hi = ~N;
+                const unsigned lo = s.uid[i];
+                if ((hi & mhi) != phi || (lo & mlo) != plo) continue;
+                const unsigned d = on_id ? (lo >> shift) & 0xffu : (unsigned)((hi >> shift) & 0xffu);
+                atomicAdd(&hist[d], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {  // the bin holding rank k, from the smallest digit up
+                const int lane = threadIdx.x;
+                unsigned v[8], tot = 0;
+                for (int j = 0; j < 8; ++j) tot += (v[j] = hist[lane * 8 + j]);
+                unsigned incl = tot;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                const unsigned k = s_k;
+                unsigned before = incl - tot;
+                const bool mine = before < k && k <= incl;
+                if (mine) {
+                    int j = 0;
+                    while (before + v[j] < k) before += v[j++];
+                    const unsigned d = (unsigned)(lane * 8 + j);
+                    s_k = k - before;
+                    if (on_id) {
+                        s_plo |= d << shift;
+                        s_mlo |= 0xffu << shift;
+                    } else {
+                        s_phi |= (unsigned long long)d << shift;
+                        s_mhi |= 0xffull << shift;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // the selected donors after the zeros: every donor, or those with keys up to T
+    const unsigned long long thi = s_phi;
+    const unsigned tlo = s_plo;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long N = s.N[i];
+        if (N < 2) continue;
+        const unsigned long long hi = ~N;
+        const unsigned lo = s.uid[i];
+        if (take_all || hi < thi || (hi == thi && lo <= tlo))
+            r[atomicAdd(&s_m, 1u)] = SortRec{hi, lo, (uint32_t)i};
+    }
+    __syncthreads();
+    const unsigned m = s_m;
+    const unsigned npa = m - nz < np ? m - nz : np;  // = np (keys are unique); never read past the donors
     unsigned np2 = 1;
     while (np2 < m) np2 <<= 1;
     for (unsigned i = m + threadIdx.x; i < np2; i += blockDim.x) r[i] = SortRec{~0ull, ~0u, ~0u};
@@ -164,8 +238,7 @@ __global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *
             __syncthreads();
         }
     }
-    const unsigned np = nz < nd ? nz : nd;
-    for (unsigned q = threadIdx.x; q < np; q += blockDim.x) {
+    for (unsigned q = threadIdx.x; q < npa; q += blockDim.x) {
         const uint32_t z = r[q].val, d = r[nz + q].val;
         s.rw2[z] = s.rw2[d];
         s.rd3[z] = s.rd3[d];
@@ -177,7 +250,7 @@ __global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *
         s.N[z] = Nd / 2;
         s.N[d] = Nd - Nd / 2;
     }
-    if (threadIdx.x == 0 && np) atomicAdd(&st->n_recycled, (unsigned long long)np);
+    if (threadIdx.x == 0) atomicAdd(&st->n_recycled, (unsigned long long)npa);
 }
 
 bool recycle_small(const sdm_ctx *c) { return c->n_sd <= kSmemSort; }
