@@ -461,7 +461,11 @@ __global__ void __launch_bounds__(kBigBlock)
             }
         }
         __syncthreads();
-        block_sort(skey, spk, npow2);
+        // already in id order (a one-cell domain keeps its storage order
+        // through the counting sort): no sort
+        bool ordered = true;
+        for (int t = threadIdx.x; t + 1 < n; t += blockDim.x) ordered &= spk[t] < spk[t + 1];
+        if (!__syncthreads_and(ordered)) block_sort(skey, spk, npow2);
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             const uint32_t pi = (uint32_t)(spk[t] & 0xffffffffu);
             const uint32_t o = beg + t;

@@ -163,7 +163,10 @@ __global__ void k_move(SdArrays s, int64_t n, MoveParams p, const double *rhod, 
         if (g.nz > 0) s.z[q] = z;
         const int nc = cell_of(g, x, y, z);
         newcell[q] = (uint32_t)nc;
-        slot[q] = atomicAdd(count + nc, 1u);
+        // one cell: the slot is the storage index, so the counting sort keeps
+        // the order (the coalescence gather then finds it in id order)
+        const uint32_t sl = atomicAdd(count + nc, 1u);
+        slot[q] = g.n_cells == 1 ? (uint32_t)q : sl;
     }
     // rainfall: warp-reduce, one atomic per warp that saw any
 #pragma unroll
