@@ -69,3 +69,27 @@ def test_euler_step_rejects_relaxation_without_profiles():
     with pytest.raises(sdm.SdmError) as e:
         sdm.sdm_euler_step(p.ctx, th, rv, w.rhoCx, None, w.rhoCz, th0=np.zeros(13), rv0=np.zeros(13), tau_rlx=0.0)
     assert e.value.status == 1
+
+
+def test_euler_step_full_size_2d():
+    """The full 75 x 75 case, in the launch configuration the bench uses
+    (device fields): 30 Eulerian steps against the oracle's, every cell."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    w = workloads.icmw_2d()
+    th0, rv0 = profiles(w)
+    p = sdm.Particles(w.cfg, w.th, w.rv, w.rhod, w.rhoCx, None, w.rhoCz)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(5)
+    th_h = w.th + rng.uniform(-0.3, 0.3, w.th.shape)
+    rv_h = w.rv * rng.uniform(0.97, 1.03, w.rv.shape)
+    th, rv, Cx, Cz = dev(th_h), dev(rv_h), dev(w.rhoCx), dev(w.rhoCz)
+    th_o, rv_o = th_h.ravel().copy(), rv_h.ravel().copy()
+    for _ in range(30):
+        p.euler_step(th, rv, Cx, None, Cz, th0, rv0)
+        th_o = oracle.relax(w.cfg, oracle.upwind(w.cfg, th_o, w.rhod, w.rhoCx, None, w.rhoCz), th0)
+        rv_o = oracle.relax(w.cfg, oracle.upwind(w.cfg, rv_o, w.rhod, w.rhoCx, None, w.rhoCz), rv0)
+    torch.cuda.synchronize()
+    assert_close("theta", th.cpu().numpy().ravel(), th_o)
+    assert_close("r_v", rv.cpu().numpy().ravel(), rv_o)
+    p.close()
