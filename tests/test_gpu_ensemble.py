@@ -203,3 +203,35 @@ def test_autotune_keeps_state_and_picks_a_launchable_shape(precision):
             # another tile split rounds the member sums differently; activating
             # droplets amplify that (up to ~1e-11 per ulp of the ambient state)
             np.testing.assert_allclose(a["rw2"], b["rw2"], rtol=1e-9)
+
+
+def test_full_size_ensemble_members_same_alone():
+    """The benchmarked ensemble itself (256 ragged members, N_sd log-uniform
+    in [1e3, 1e6], about 3.4e7 super-droplets, mixed precision, graph
+    replay): after two steps with the parcels' rho_d, sampled members are bit
+    for bit what they are when stepped alone."""
+    members = workloads.ensemble_members(256, seed=0)
+    opts = dict(adve=0, sedi=0, cond=1, coal=1, RH_max=44.0, sstp_cond=10, sstp_coal=10)
+    n_sd = sum(m["n_sd"] for m in members)
+    ens = Ensemble(precision="mixed", max_sd=n_sd + 1024, max_members=len(members))
+    ids = [ens.add(m) for m in members]
+    ens.use_graph(True)
+    for t in (1.0, 2.0):
+        r = workloads.parcel_rhod(members, t)
+        ens.step(opts, rhod={ids[k]: v for k, v in r.items()})
+        ens.wait()
+    rng = np.random.default_rng(0)
+    picks = [int(np.argmax([m["n_sd"] for m in members]))] + rng.choice(len(members), 3, replace=False).tolist()
+    for k in picks:
+        m = members[k]
+        alone = Ensemble(precision="mixed", max_sd=m["n_sd"], max_members=1)
+        a = alone.add(m)
+        for t in (1.0, 2.0):
+            r = workloads.parcel_rhod([m], t)
+            alone.step(opts, rhod={a: r[0]} if 0 in r else None)
+            alone.wait()
+        for name in ("N", "rw2", "rd3", "kappa"):
+            assert np.array_equal(ens.attr(ids[k], name, m["n_sd"]), alone.attr(a, name, m["n_sd"])), (k, name)
+        assert np.array_equal(ens.fields([ids[k]])[1], alone.fields([a])[1])
+        alone.close()
+    ens.close()
