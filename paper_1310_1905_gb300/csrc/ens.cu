@@ -716,7 +716,7 @@ sdm_status sdm_ens_create(const sdm_ens_opts *o, void *stream, sdm_ens **out) {
         e->own_stream = true;
     }
     const size_t n = (size_t)e->cap_sd, nm = (size_t)e->cap_members;
-    const int64_t tiles_rs = (e->cap_sd + 4095) / 4096;
+    const int64_t tiles_rs = (e->cap_sd + kRsTileRecords - 1) / kRsTileRecords;
     auto A = [&](void **p, size_t bytes) {
         if (r == cudaSuccess) r = cudaMalloc(p, bytes);
     };

@@ -15,8 +15,8 @@
 namespace sdm {
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 16;                       // items per thread
-constexpr int kRsTile = kRsThreads * kRsItems;     // 4096 records per tile
+constexpr int kRsItems = kRsTileRecords / kRsThreads;  // items per thread
+constexpr int kRsTile = kRsTileRecords;                // records per tile
 constexpr int kRsWarps = kRsThreads / 32;
 
 template <class K>
