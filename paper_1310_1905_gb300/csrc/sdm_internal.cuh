@@ -352,7 +352,7 @@ cudaError_t launch_sd_conc(sdm_ctx *c);
 constexpr int kMaxSpectrumBins = 256;
 // records per tile of the ensemble's radix sort: the histogram table its
 // callers allocate holds 256 counts per tile of this size
-constexpr int kRsTileRecords = 4096;
+constexpr int kRsTileRecords = 2048;
 cudaError_t launch_upwind(const double *old, double *out, const double *rhod, const double *Cx, const double *Cy,
                           const double *Cz, const Grid &g, cudaStream_t st);
 cudaError_t launch_relax(double *psi, const double *psi0, const Grid &g, double tau_rlx, double z_rlx,
