@@ -15,6 +15,10 @@
 namespace sdm {
 
 constexpr int kRsThreads = 256;
+// one thread per digit bin in the histogram and in the scatter's per-digit
+// bookkeeping, and whole items per thread in a tile
+static_assert(kRsThreads == 256, "the kernels index the 256 digit bins by thread");
+static_assert(kRsTileRecords % kRsThreads == 0, "a tile is a whole number of items per thread");
 constexpr int kRsItems = kRsTileRecords / kRsThreads;  // items per thread
 constexpr int kRsTile = kRsTileRecords;                // records per tile
 constexpr int kRsWarps = kRsThreads / 32;
