@@ -160,7 +160,7 @@ def make_domain(cfg: dict) -> Domain:
     d.dx, d.dy, d.dz = cfg.get("dx", 1.0), cfg.get("dy", 1.0), cfg.get("dz", 1.0)
     d.dt = cfg.get("dt", 1.0)
     d.sd_conc = cfg.get("sd_conc", 64)
-    d.kernel = {"geometric": 0, "golovin": 1}[cfg.get("kernel", "geometric")]
+    d.kernel = {"geometric": 0, "golovin": 1, "long": 2}[cfg.get("kernel", "geometric")]
     d.golovin_b = cfg.get("golovin_b", 0.0)
     d.init_dist = {"lognormal": 0, "exponential": 1}[cfg.get("init_dist", "lognormal")]
     d.exp_mean_volume = cfg.get("exp_mean_volume", 0.0)

@@ -636,7 +636,21 @@ static double kernel_K(const orc_domain *d, const orc_thermo *t, double rw2a, do
     }
     double ra = sqrt(rw2a), rb = sqrt(rw2b);
     double dv = fabs(orc_vterm(rw2a, t) - orc_vterm(rw2b, t));
-    return PI * (ra + rb) * (ra + rb) * dv;
+    double E = 1.0;
+    if (d->kernel == 2) {
+        /* hydrodynamic collection efficiency after Long (1974), a formula
+         * standing in for the tabulated ones the paper cites (Sec. 5.1.4),
+         * READING: R the larger, r the smaller radius; E = 1 for R >= 50 um,
+         * else 4.5e4 R^2 (1 - 3e-4/r) with R, r in cm (4.5e8 R^2 (1 - 3e-6/r)
+         * in m), floored at 1e-3 and capped at 1 */
+        double R = ra > rb ? ra : rb, r = ra > rb ? rb : ra;
+        if (R < 50e-6) {
+            E = 4.5e8 * R * R * (1.0 - 3e-6 / r);
+            if (E < 1e-3) E = 1e-3;
+            if (E > 1.0) E = 1.0;
+        }
+    }
+    return E * (PI * (ra + rb) * (ra + rb) * dv);
 }
 
 /* gamma collision events of all min(N_i, N_j) particles (Sec. 5.1.4; gamma

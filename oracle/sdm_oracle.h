@@ -29,7 +29,7 @@ typedef struct {
     int nx, ny, nz;                /* cells per dimension; 0 = dimension absent */
     double dx, dy, dz, dt;         /* grid steps [m], timestep [s]             */
     int sd_conc;                   /* super-droplets per cell per kappa group  */
-    int kernel;                    /* 0 geometric (E = 1), 1 Golovin            */
+    int kernel;                    /* 0 geometric (E = 1), 1 Golovin, 2 Long    */
     double golovin_b;              /* Golovin constant [s^-1]                  */
     int init_dist;                 /* 0 lognormal dry modes, 1 exp. wet volume  */
     double exp_mean_volume;        /* mean droplet volume [m^3]  (init_dist 1) */
