@@ -62,7 +62,7 @@ typedef struct {
     double rm, sigma, n_stp, kappa;
 } sdm_lognormal;
 
-enum { SDM_KERNEL_GEOMETRIC = 0, SDM_KERNEL_GOLOVIN = 1 };
+enum { SDM_KERNEL_GEOMETRIC = 0, SDM_KERNEL_GOLOVIN = 1, SDM_KERNEL_LONG = 2 };
 enum { SDM_INIT_LOGNORMAL = 0, SDM_INIT_EXPONENTIAL = 1 };
 enum { SDM_PRECISION_FP64 = 0, SDM_PRECISION_MIXED = 1 };
 enum { SDM_BACKEND_SERIAL = 0, SDM_BACKEND_OPENMP = 1, SDM_BACKEND_CUDA = 2 };
@@ -73,8 +73,12 @@ enum { SDM_SOLVER_BISECT = 0, SDM_SOLVER_FAST = 1 };
  *   one cell); dx, dy, dz [m]; dt [s].
  * sd_conc: super-droplets per cell per distinct kappa at initialisation
  *   (sd_conc_mean); they are placed uniformly at random within each cell.
- * kernel: SDM_KERNEL_GEOMETRIC (the paper's kernel_t::geometric, E = 1) or
- *   SDM_KERNEL_GOLOVIN (K = golovin_b (V_i + V_j), for the box test).
+ * kernel: SDM_KERNEL_GEOMETRIC (the paper's kernel_t::geometric, E = 1),
+ *   SDM_KERNEL_GOLOVIN (K = golovin_b (V_i + V_j), for the box test) or
+ *   SDM_KERNEL_LONG (the geometric kernel times the Long 1974 efficiency:
+ *   E = 1 for a larger radius R >= 50 um, else 4.5e8 R^2 (1 - 3e-6 / r) in
+ *   SI units held within [1e-3, 1]; the paper tabulates its efficiencies,
+ *   Sec. 5.1.4).  Any other value: SDM_EINVAL.
  * init_dist: SDM_INIT_LOGNORMAL uses modes[0..n_modes); SDM_INIT_EXPONENTIAL
  *   draws wet volumes from an exponential law of mean exp_mean_volume [m^3]
  *   with exp_n0 droplets per m^3 and no dry mass (box test).

@@ -370,6 +370,7 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
                     const float va = vterm_f((float)Ra, (float)t.nu, (float)t.cX);
                     const float vb = vterm_f((float)Rb, (float)t.nu, (float)t.cX);
                     K = (float)phys::pi * (ra + rb) * (ra + rb) * fabsf(va - vb);
+                    if (p.kernel == SDM_KERNEL_LONG) K = long_Ef(ra, rb) * K;
                 }
                 const float Pf = (float)Nmax * K * (float)dtpp / (float)md.dV * (float)scale;
                 P = Pf;
@@ -383,6 +384,7 @@ __global__ void k_ens_pairs(SdArrays s, MemberDev *M, const uint32_t *aux, const
                     const double ra = sqrt(Ra), rb = sqrt(Rb);
                     const double dv = fabs(vterm(Ra, t.nu, t.cX) - vterm(Rb, t.nu, t.cX));
                     K = phys::pi * (ra + rb) * (ra + rb) * dv;
+                    if (p.kernel == SDM_KERNEL_LONG) K = long_E(ra, rb) * K;
                 }
                 P = (double)Nmax * K * dtpp / md.dV * scale;
             }
@@ -695,7 +697,7 @@ sdm_status sdm_ens_create(const sdm_ens_opts *o, void *stream, sdm_ens **out) {
     *out = nullptr;
     if (!(o->dt > 0) || o->max_sd < 1 || o->max_members < 1 || o->max_sd >= (1LL << 31))
         return efail(nullptr, SDM_EINVAL, "need dt > 0, 1 <= max_sd < 2^31, max_members >= 1");
-    if (o->kernel != SDM_KERNEL_GEOMETRIC && o->kernel != SDM_KERNEL_GOLOVIN)
+    if (o->kernel != SDM_KERNEL_GEOMETRIC && o->kernel != SDM_KERNEL_GOLOVIN && o->kernel != SDM_KERNEL_LONG)
         return efail(nullptr, SDM_EINVAL, "unknown collision kernel");
     if (o->precision != SDM_PRECISION_FP64 && o->precision != SDM_PRECISION_MIXED)
         return efail(nullptr, SDM_EINVAL, "unknown precision mode");

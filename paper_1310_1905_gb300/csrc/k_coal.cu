@@ -96,8 +96,9 @@ __device__ __forceinline__ unsigned long long p_bits(double P) {
     return (unsigned long long)__double_as_longlong(P);
 }
 
-// collection kernel: geometric (E = 1) or Golovin; ra = sqrt(rw2a), rb =
+// collection kernel: geometric (E = 1), Long (E = long_E) or Golovin; ra = sqrt(rw2a), rb =
 // sqrt(rw2b), kept per super-droplet by the callers
+template <bool EFF = true>
 __device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, double ra, double rw2b,
                                            double rb, double vta, double vtb) {
     if (p.kernel == SDM_KERNEL_GOLOVIN) {
@@ -106,7 +107,8 @@ __device__ __forceinline__ double kernel_K(const CoalParams &p, double rw2a, dou
         return p.golovin_b * (Va + Vb);
     }
     const double dv = fabs(vta - vtb);
-    return phys::pi * (ra + rb) * (ra + rb) * dv;
+    const double K = phys::pi * (ra + rb) * (ra + rb) * dv;
+    return EFF && p.kernel == SDM_KERNEL_LONG ? long_E(ra, rb) * K : K;
 }
 
 // Mixed-precision mode: terminal velocities, the kernel and P in FP32, a
@@ -116,6 +118,9 @@ __device__ __forceinline__ double vt_of(const CoalParams &p, double rw2, double 
     return p.mixed ? (double)vterm_f((float)rw2, (float)nu, (float)cX) : vterm_r(rw2, r, nu, cX);
 }
 
+// EFF = false compiles the Long efficiency out (the variants that never see
+// SDM_KERNEL_LONG)
+template <bool EFF = true>
 __device__ __forceinline__ double prob(const CoalParams &p, unsigned long long Nmax, double rwa, double ra,
                                        double rwb, double rb, double va, double vb, double dtpp, double scale) {
     if (p.mixed) {
@@ -126,10 +131,11 @@ __device__ __forceinline__ double prob(const CoalParams &p, unsigned long long N
         } else {
             const float ra = sqrtf((float)rwa), rb = sqrtf((float)rwb);
             K = (float)phys::pi * (ra + rb) * (ra + rb) * fabsf((float)va - (float)vb);
+            if (EFF && p.kernel == SDM_KERNEL_LONG) K = long_Ef(ra, rb) * K;
         }
         return (double)((float)Nmax * K * (float)dtpp / (float)p.g.dV * (float)scale);
     }
-    const double K = kernel_K(p, rwa, ra, rwb, rb, va, vb);
+    const double K = kernel_K<EFF>(p, rwa, ra, rwb, rb, va, vb);
     return (double)Nmax * K * dtpp / p.g.dV * scale;
 }
 
@@ -221,8 +227,8 @@ struct SmemAcc {
 };
 
 // cells of up to 32 R super-droplets, one warp each, R per lane.  EXT:
-// multiple coalescence or adaptive substeps on; the paper's scheme runs a
-// copy without their code.
+// multiple coalescence, adaptive substeps or the Long kernel on; the
+// paper's scheme runs a copy without their code.
 template <int R, bool EXT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_coal_warp(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     warp_sort<R>(v, lane);
     const double nu = amb[2 * c], cX = amb[2 * c + 1];
-    const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
+    const bool geo = p.kernel != SDM_KERNEL_GOLOVIN;  // kernels of terminal velocity
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int q = R * lane + r;
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     const int a = (int)(ka.pk & 0xffu), b = (int)(kb.pk & 0xffu);
                     const unsigned long long Na = W.N[a], Nb = W.N[b];
                     const unsigned long long Nmax = Na > Nb ? Na : Nb, Nmin = Na > Nb ? Nb : Na;
-                    const double P = prob(p, Nmax, W.rw2[a], W.r[a], W.rw2[b], W.r[b], W.vt[a], W.vt[b], dtpp,
+                    const double P = prob<EXT>(p, Nmax, W.rw2[a], W.r[a], W.rw2[b], W.r[b], W.vt[a], W.vt[b], dtpp,
                                           scale);
                     n_pairs++;
                     const unsigned long long pb = p_bits(P);
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(kBigBlock)
         if (threadIdx.x == 0) s_maxp = 0;
         __syncthreads();
         const double nu = amb[2 * c], cX = amb[2 * c + 1];
-        const bool geo = p.kernel == SDM_KERNEL_GEOMETRIC;
+        const bool geo = p.kernel != SDM_KERNEL_GOLOVIN;  // kernels of terminal velocity
         GlobalAcc A{dst, beg};
         if (threadIdx.x == 0) s_sstp = p.sstp;
         if (p.coal && p.adapt > 0) {  // adaptive_sstp from a block reduction
@@ -620,7 +626,7 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     // records per lane: cells hold sd_conc on average and spread around it
     // as super-droplets move, so the warp path covers twice the mean
     const int per_cell = c->G * c->oi.sd_conc;
-    const bool ext = p.multi || p.adapt > 0;
+    const bool ext = p.multi || p.adapt > 0 || p.kernel == SDM_KERNEL_LONG;
     auto launch = [&](auto kern) {
         kern<<<nb, kWarpsPerBlock * 32, 0, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p, c->bigcells,
                                                         c->dstats);

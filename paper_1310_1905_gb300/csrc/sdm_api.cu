@@ -346,7 +346,7 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
     if (!(oi->dx > 0 && oi->dy > 0 && oi->dz > 0 && oi->dt > 0))
         return fail(nullptr, SDM_EINVAL, "dx, dy, dz and dt must be positive");
     if (oi->sd_conc < 1) return fail(nullptr, SDM_EINVAL, "sd_conc must be >= 1");
-    if (oi->kernel != SDM_KERNEL_GEOMETRIC && oi->kernel != SDM_KERNEL_GOLOVIN)
+    if (oi->kernel != SDM_KERNEL_GEOMETRIC && oi->kernel != SDM_KERNEL_GOLOVIN && oi->kernel != SDM_KERNEL_LONG)
         return fail(nullptr, SDM_EINVAL, "unknown collision kernel");
     if (oi->precision != SDM_PRECISION_FP64 && oi->precision != SDM_PRECISION_MIXED)
         return fail(nullptr, SDM_EINVAL, "unknown precision mode");

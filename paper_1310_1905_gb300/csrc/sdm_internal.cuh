@@ -190,6 +190,27 @@ SDM_HD float vterm_f(float rw2, float nu, float cX) {
     return Re * nu / (2.0f * r);
 }
 
+// Collection efficiency of the Long (1974) kernel (the paper's collision
+// efficiencies come from tables, Sec. 5.1.4; this closed form stands in):
+// with R the larger and r the smaller radius, E = 1 for R >= 50 um, else
+// 4.5e8 R^2 (1 - 3e-6 / r) in SI units, held within [1e-3, 1].  Products
+// and one quotient only, so no contraction changes its rounding.
+SDM_HD double long_E(double ra, double rb) {
+    const double R = ra > rb ? ra : rb, r = ra > rb ? rb : ra;
+    if (R >= 50e-6) return 1.0;
+    double E = 4.5e8 * R * R * (1.0 - 3e-6 / r);
+    if (E < 1e-3) E = 1e-3;
+    if (E > 1.0) E = 1.0;
+    return E;
+}
+
+SDM_HD float long_Ef(float ra, float rb) {
+    const float R = ra > rb ? ra : rb, r = ra > rb ? rb : ra;
+    if (R >= 50e-6f) return 1.0f;
+    float E = 4.5e8f * R * R * (1.0f - 3e-6f / r);
+    return E < 1e-3f ? 1e-3f : (E > 1.0f ? 1.0f : E);
+}
+
 // 24 random bits plus one half, times 2^-24: open (0,1) in FP32
 SDM_HD float u01f(uint64_t v) { return ((float)(uint32_t)(v >> 40) + 0.5f) * 5.9604645e-8f; }
 

@@ -25,7 +25,7 @@ class SdmError(RuntimeError):
 
 STATUS = {0: "SDM_OK", 1: "SDM_EINVAL", 2: "SDM_ENOMEM", 3: "SDM_ECUDA", 4: "SDM_ETIMEOUT",
           5: "SDM_ENUMERIC", 6: "SDM_ESTATE", 7: "SDM_ENOTSUP"}
-KERNEL = {"geometric": 0, "golovin": 1}
+KERNEL = {"geometric": 0, "golovin": 1, "long": 2}
 INIT = {"lognormal": 0, "exponential": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 BACKEND = {"serial": 0, "openmp": 1, "cuda": 2}
