@@ -2,11 +2,13 @@
 with sstp_cond condensation substeps + step_async with recycling,
 advection, sedimentation, regrouping and sstp_coal coalescence substeps).
 
-Default workload: the 2D prescribed-flow kinematic cloud, 75 x 75 cells of
-20 m, 64 super-droplets per cell (360 000), bimodal ammonium-sulphate
-aerosol, geometric kernel, dt = 1 s, 10/10 substeps, FP64 state.
+Default workload: the large 3D kinematic domain, 128 x 128 x 128 cells of
+20 m, 32 super-droplets per cell (67 108 864), bimodal ammonium-sulphate
+aerosol, uniform updraft of 1 m/s with per-column perturbations, geometric
+kernel, dt = 1 s, 10/10 substeps, FP64 state.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload updraft_3d|icmw_2d|golovin_box|ensemble|serve]
 
 Prints one JSON line.  Metric: super-droplet-steps per second over all
 ranks.  ``value`` is device time (CUDA events on the library's stream, L2
@@ -14,12 +16,19 @@ flushed between timed steps, inputs resident in HBM); ``e2e`` is the same
 metric through the public API with host buffers (theta and r_v copied in and
 out every step), wall clock.  Multi-GPU runs are independent replicas (one
 domain per rank, weak scaling).
+
+``--impl reference`` times the CPU oracle (serial and cell-parallel OpenMP
+builds of the same source) on a bounded sample of the same workload, the way
+the paper times its back-ends (Sec. 6): whole runs of a short and a long
+step count, each the shortest of three, per step = (long - short) / (steps
+between them).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,18 +44,28 @@ import workloads  # noqa: E402
 METRIC = "super-droplet-steps/s (coal+cond)"
 UNIT = "SD-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 arithmetic peak of one GB300 derived from unit counts and clocks:
-# 1.25 TFLOP/s nominal at the 2070 MHz boost clock over 152 SMs is 2 DFMA
-# (4 FP64 flops) per SM per clock
+# FP64 arithmetic of one SM per clock on this part: 1.25 TFLOP/s nominal at
+# the 2070 MHz boost clock over 152 SMs is 2 DFMA (4 FP64 flops) per SM per
+# clock; the bench also measures the throughput (sdm_probe_device) and takes
+# that as the peak
 FP64_FLOPS_PER_SM_CLK = 4.0
-N_SM = 152
-# ncu, k_condense: the FP64 flops it executes (2 DFMA + DADD + DMUL) per
+# Algorithmic FP64 work of the condensation solve per super-droplet and
+# substep: about 4-6 evaluations of the growth rate of a safeguarded Newton
+# solve at 60-100 flops each (an exponential and a few divisions included),
+# 3-6 kflop per SD-step over 10 substeps; the midpoint, 450 flops per
+# SD-substep, is the per-unit figure the roofline line uses
+COND_ALGO_FLOPS_PER_SD_SUBSTEP = 450.0
+# Algorithmic HBM bytes per SD-step of the coalescence + condensation step:
+# condensation reads N, r_w^2, r_d^3, kappa and writes r_w^2 (40 B);
+# coalescence reads those and the id and writes N, r_w^2, r_d^3, kappa
+# (68 B); the regrouping reads the cell and moves the state (116 B in 2D,
+# 132 B in 3D)
+HBM_BYTES_PER_SD_STEP = {"icmw_2d": 40 + 68 + 116, "updraft_3d": 40 + 68 + 132, "golovin_box": 68 + 116}
+# ncu on k_condense: the FP64 flops it executes (2 DFMA + DADD + DMUL) per
 # SD-substep, its DRAM bytes read + written per launch per super-droplet and
 # the share of active cycles its FP64 pipe is busy, with the capture they
-# come from (profiles/k_condense_icmw_2d_fp64.md,
-# profiles/kernels_updraft_3d_64cubed_fp64.md).  Mixed precision too is
-# bound by its FP64 part (the solves near activation): its FP32 work is
-# about 1 % of the FP32 peak.
+# come from.  Mixed precision too is bound by its FP64 part (the solves near
+# activation): its FP32 work is about 1 % of the FP32 peak.
 COND_FP64 = {
     ("icmw_2d", "fp64"): dict(flops_per_sd_substep=649.85, dram_bytes_per_sd=11.835e6 / 360000,
                               fp64_pipe_active=0.7175, capture="2D case, 360 000 SDs, one launch"),
@@ -66,7 +85,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="icmw_2d", choices=["icmw_2d", "updraft_3d", "golovin_box", "ensemble", "serve"])
+    ap.add_argument("--workload", default="updraft_3d", choices=["icmw_2d", "updraft_3d", "golovin_box", "ensemble", "serve"])
     ap.add_argument("--members", type=int, default=256)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -164,6 +183,7 @@ def run_gpu(args, rank: int, world: int):
     rhod = torch.tensor(w.rhod, dtype=torch.float64, device="cuda")
     Cs = [None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
           for a in (w.rhoCx, w.rhoCy, w.rhoCz)]
+    device = sdm.sdm_probe_device(2.0)  # SM count and FP64 throughput, before the workload
     p = sdm.Particles(w.cfg, th, rv, rhod, *Cs, stream=stream.cuda_stream, precision=args.precision)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -220,7 +240,7 @@ def run_gpu(args, rank: int, world: int):
     sdm.sdm_timing_enable(p.ctx, False)
     t_max = dist_max(t_dev, world)
     stats = p.stats()
-    res = dict(t_dev=t_max, timing=tim, clocks=clk, stats=stats, n_sd=p.n_sd, w=w)
+    res = dict(t_dev=t_max, timing=tim, clocks=clk, stats=stats, n_sd=p.n_sd, w=w, device=device)
     # ---- e2e through the public API with host buffers
     if not args.no_e2e:
         th_h, rv_h = w.th.copy(), w.rv.copy()
@@ -385,27 +405,88 @@ def whole_job_value(n_sd_per_rank: int, steps: int, world: int, t_max: float) ->
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample(steps: int, warmup: int, nx: int = 4):
-    """The CPU oracle as it stands on a bounded sample of the workload: the
-    same 2D case restricted to nx of the 75 columns (nx x 75 cells, 64
-    SD/cell), full steps; single thread."""
+def oracle_sample_workload(name: str, seed: int = 0, cells: int = 128):
+    """A bounded sample of the workload for the CPU oracle: the 3D domain's
+    full columns on a 2 x 2 horizontal patch (2 x 2 x 128 cells of 32 SDs;
+    the flow has no horizontal component, so its columns are independent),
+    4 of the 2D case's 75 columns, or the whole one-cell box."""
+    if name == "updraft_3d":
+        return workloads.updraft_3d(nx=2, ny=2, nz=cells, seed=seed)
+    if name == "icmw_2d":
+        return workloads.icmw_2d(nx=4, seed=seed)
+    return workloads.golovin_box(seed=seed)
+
+
+def oracle_timing(name: str, k_short: int, k_long: int, omp: bool, repeats: int = 3, cells: int = 128) -> dict:
+    """The oracle as it stands, timed as the paper times its back-ends
+    (Sec. 6): whole runs (initialisation + steps) of k_short and of k_long
+    steps, each the shortest of ``repeats``, and per step
+    (long - short) / (k_long - k_short), which cancels the initialisation.
+    The Eulerian step of the kinematic driver runs between the steps, as on
+    the GPU, and is left out of the run times."""
     import oracle
-    w = workloads.icmw_2d(nx=nx)
-    th0, rv0 = w.th.mean(axis=0), w.rv.mean(axis=0)
-    o = oracle.Oracle(w.cfg)
-    o.init(w.th, w.rv, w.rhod)
-    for _ in range(warmup):
-        o.euler_step(w.rhoCx, None, w.rhoCz, th0, rv0)
-        o.step_sync(w.opts)
-        o.step_async(w.opts, w.rhoCx, None, w.rhoCz)
-    dt = 0.0
-    for _ in range(steps):
-        o.euler_step(w.rhoCx, None, w.rhoCz, th0, rv0)  # the driver's part: not timed, as on the GPU
+    w = oracle_sample_workload(name, cells=cells)
+    threads = oracle.threads(0, omp=omp)
+    relax = w.name == "icmw_2d"
+    axes = tuple(range(np.ndim(w.th) - 1))
+    th0, rv0 = (w.th.mean(axis=axes), w.rv.mean(axis=axes)) if relax else (None, None)
+
+    def run(k):
+        o = oracle.Oracle(w.cfg, omp=omp)
         t0 = time.perf_counter()
-        o.step_sync(w.opts)
-        o.step_async(w.opts, w.rhoCx, None, w.rhoCz)
-        dt += time.perf_counter() - t0
-    return w.n_sd * steps / dt, w.n_sd, dt
+        o.init(w.th, w.rv, w.rhod)
+        t = time.perf_counter() - t0
+        for _ in range(k):
+            if w.name != "golovin_box":
+                o.euler_step(w.rhoCx, w.rhoCy, w.rhoCz, th0, rv0)
+            t0 = time.perf_counter()
+            if w.opts.get("cond", 1):
+                o.step_sync(w.opts)
+            o.step_async(w.opts, w.rhoCx, w.rhoCy, w.rhoCz)
+            t += time.perf_counter() - t0
+        return t
+
+    t_short = min(run(k_short) for _ in range(repeats))
+    t_long = min(run(k_long) for _ in range(repeats))
+    per_step = max(t_long - t_short, 1e-9) / (k_long - k_short)
+    return dict(value=w.n_sd / per_step, ms_per_step=per_step * 1e3, n_sd=w.n_sd, threads=threads,
+                t_short=t_short, t_long=t_long, k_short=k_short, k_long=k_long, repeats=repeats,
+                sample=f"{w.name}: {w.cfg['nx']}x{w.cfg['ny']}x{w.cfg['nz']} cells x {w.cfg['sd_conc']} SD "
+                       f"({w.n_sd} SDs) of the same workload")
+
+
+def host_cpu() -> dict:
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return dict(nproc=os.cpu_count(), model=model, arch=platform.machine())
+
+
+def cpu_baseline(name: str, k_short: int, k_long: int, cells: int = 128) -> dict:
+    """Serial and cell-parallel oracle on the same sample; the OpenMP figure
+    (all host cores) is the line's value, the serial one rides along."""
+    par = oracle_timing(name, k_short, k_long, omp=True, cells=cells)
+    ser = oracle_timing(name, k_short, k_long, omp=False, cells=cells)
+    how = (f"shortest of {par['repeats']} whole runs of {k_short} and of {k_long} steps from initialisation, "
+           f"per step = (long - short)/{k_long - k_short}")
+    return dict(value=par["value"], unit=UNIT, cores=par["threads"], kind="oracle",
+                sample=f"{par['sample']}; {how}; OpenMP cell-parallel build, {par['threads']} threads",
+                ms_per_step=par["ms_per_step"], host=host_cpu(),
+                serial=dict(value=ser["value"], unit=UNIT, cores=1, ms_per_step=ser["ms_per_step"],
+                            sample=f"{ser['sample']}; {how}; serial build"))
 
 
 def peaks():
@@ -427,18 +508,18 @@ def main():
 
     if args.impl == "reference":
         if rank == 0:
-            # every step a bounded sample of the workload: 4 of its 75 columns
-            v, n_sd, dt = oracle_sample(args.steps, args.warmup)
-            w = make_workload(args.workload, 0)
-            line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                        warmup=args.warmup, ms_per_step=w.n_sd / v * 1e3, higher_is_better=True,
+            name = args.workload if args.workload in ("updraft_3d", "icmw_2d", "golovin_box") else "updraft_3d"
+            k_short = max(1, args.warmup)
+            cb = cpu_baseline(name, k_short, k_short + max(1, args.steps), cells=args.cells)
+            line = dict(impl="reference", metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus,
+                        steps=args.steps, warmup=args.warmup, ms_per_step=cb["ms_per_step"], higher_is_better=True,
                         scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                        config=workload_desc(w),
-                        cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle",
-                                          sample=f"2D case, 4x75 cells x 64 SD ({n_sd} SDs), "
-                                                 f"{args.steps} full steps after {args.warmup} warm-up, "
-                                                 f"{dt:.1f} s, serial"),
-                        e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                        config=dict(workload=cb["sample"].split(";")[0], of=workload_desc(
+                            make_workload(name, 0, args.cells))["workload"],
+                            note="a bounded sample of the workload, normalised per SD-step (the cost is linear "
+                                 "in the super-droplets, Sec. 6); ms_per_step is the sample's own"),
+                        cpu_baseline=cb,
+                        e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
             print(json.dumps(line), flush=True)
         if world > 1:
             import torch.distributed as dist
@@ -494,42 +575,60 @@ def main():
     value = whole_job_value(res["n_sd"], args.steps, world, res["t_dev"])
     tim = res["timing"]
     pk = peaks()
-    # dominant kernel: condensation, bound by FP64 arithmetic.  Its FP64 work
-    # per SD-substep (2 DFMA + DADD + DMUL thread instructions) is measured
-    # with ncu on this workload (profiles/k_condense_icmw_2d_fp64.md); the
-    # bench multiplies it by the SD-substeps of one launch and divides by the
-    # launch's CUDA-event time.
+    # dominant kernel: condensation, bound by FP64 arithmetic.  achieved =
+    # the algorithmic FP64 flops of the solve per SD-substep x the
+    # SD-substeps of one launch / the launch's CUDA-event time; peak = the
+    # FP64 FMA throughput measured on this device (sustained: one launch
+    # runs for most of a step)
     cond_ms = tim["cond_ms"] / max(1, tim["cond_launches"])
     clk = res["clocks"]
+    dev = res["device"]
     sm_mhz = clk.get("sm_mhz") or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
-    fp64_peak = FP64_FLOPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    fp64_derived = FP64_FLOPS_PER_SM_CLK * dev["n_sm"] * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    fp64_peak = dev["fp64_tflops_sustained"] or dev["fp64_tflops_burst"]
     units = res["n_sd"] * w.opts["sstp_cond"]
+    hbm = pk.get("hbm_gbs", 6800.0)
+    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "of fallback 6800 GB/s"
     if (args.workload, args.precision) in COND_FP64:
         k = COND_FP64[(args.workload, args.precision)]
-        achieved = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
+        achieved = COND_ALGO_FLOPS_PER_SD_SUBSTEP * units / (cond_ms * 1e-3) / 1e12
+        executed = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
         roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
                     frac=achieved / fp64_peak, traffic=k["dram_bytes_per_sd"] * res["n_sd"],
-                    flops_per_sd_substep=k["flops_per_sd_substep"], fp64_pipe_active=k["fp64_pipe_active"],
-                    counters=k["capture"],
-                    peak_source="derived: 4 FP64 flop/SM/clk x 152 SMs x sampled SM clock (1.25 TFLOP/s nominal)")
+                    algorithmic_flops_per_sd_substep=COND_ALGO_FLOPS_PER_SD_SUBSTEP,
+                    launch_ms=cond_ms, sd_substeps_per_launch=units,
+                    peak_source="of measured: FP64 FMA chains on this device (sdm_probe_device), sustained "
+                                f"{dev['fp64_tflops_sustained']:.3f}, burst {dev['fp64_tflops_burst']:.3f} TFLOP/s",
+                    derived_peak=dict(value=fp64_derived, how=f"4 FP64 flop/SM/clk x {dev['n_sm']} SMs (device "
+                                                              f"query) x {sm_mhz:.0f} MHz (sampled)"),
+                    executed=dict(flops_per_sd_substep=k["flops_per_sd_substep"], achieved=executed,
+                                  frac=executed / fp64_peak, fp64_pipe_active=k["fp64_pipe_active"],
+                                  counters=k["capture"]))
     elif tim["cond_launches"] > 0:
         bytes_per_launch = 40.0 * res["n_sd"]
         achieved = bytes_per_launch / (cond_ms * 1e-3) / 1e9
-        hbm = pk.get("hbm_gbs", 6800.0)
         roof = dict(kernel="k_condense", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
-                    frac=achieved / hbm, traffic=None,
-                    peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6800")
+                    frac=achieved / hbm, traffic=None, peak_source=hbm_src)
     else:  # no condensation (the Golovin box): coalescence, 68 B per SD-step (read 36, write 32)
         coal_ms = tim["coal_ms"] / max(1, tim["coal_launches"])
         achieved = 68.0 * res["n_sd"] / (coal_ms * 1e-3) / 1e9
-        hbm = pk.get("hbm_gbs", 6800.0)
         roof = dict(kernel="k_coal", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                     traffic=None, note="one cell of 8192 SDs: latency-bound, the state stays in L2",
-                    peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6800")
+                    peak_source=hbm_src)
+    bps = HBM_BYTES_PER_SD_STEP.get(args.workload)
+    hbm_cc = None
+    if bps:
+        gbs = bps * value / world / 1e9
+        hbm_cc = dict(bytes_per_sd_step=bps, achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
+                      peak_source=hbm_src,
+                      what="algorithmic HBM bytes of the coal+cond step (condensation 40, coalescence 68, "
+                           "regrouping) x SD-steps/s of one GPU")
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=res["t_dev"] / args.steps * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64" if args.precision == "fp64" else "f64/f32",
-                data="synthetic", config=workload_desc(w), roofline=roof, clocks=clk,
+                data="synthetic", config=workload_desc(w), roofline=roof, hbm_coal_cond=hbm_cc, clocks=clk,
+                device=dict(n_sm=dev["n_sm"], fp64_tflops_burst=dev["fp64_tflops_burst"],
+                            fp64_tflops_sustained=dev["fp64_tflops_sustained"]),
                 gpu_launches=int(tim["launches"]),
                 phases_ms_per_step={k[:-3]: tim[k] / args.steps for k in tim
                                     if k.endswith("_ms") and k != "euler_ms"})
@@ -544,12 +643,9 @@ def main():
                            d2h_bytes_per_step=res["d2h"])
     if not args.no_cpu:
         try:
-            v, n_sd, dt = oracle_sample(8, 1, nx=8)
-            line["cpu_baseline"] = dict(value=v, unit=UNIT, cores=1, kind="oracle",
-                                        sample=f"2D case, 8x75 cells x 64 SD ({n_sd} SDs), 8 full steps "
-                                               f"after 1 warm-up, {dt:.1f} s, serial")
+            line["cpu_baseline"] = cpu_baseline(args.workload, 1, 4, cells=args.cells)
         except Exception as e:  # the oracle is a baseline, never a fallback
-            line["cpu_baseline"] = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample=f"failed: {e}")
+            line["cpu_baseline"] = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {e}")
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -345,6 +345,27 @@ sdm_status sdm_cell_sort(const uint32_t *cell, int64_t n, int32_t n_cells, uint3
 sdm_status sdm_cell_sort_noalloc(const uint32_t *cell, int64_t n, int32_t n_cells, uint32_t *perm,
                                  uint32_t *offsets, void *stream);
 
+/* ---- device probe ------------------------------------------------------- */
+
+/* What sdm_probe_device measures on the current device. */
+typedef struct {
+    int n_sm;                     /* multiprocessors (cudaDevAttrMultiProcessorCount)          */
+    int blocks;                   /* blocks of the probe launch (n_sm x resident blocks per SM) */
+    double fp64_tflops_burst;     /* FP64 FMA throughput, best of 5 launches of ~20 ms [TFLOP/s] */
+    double fp64_tflops_sustained; /* the same over back-to-back launches for sustained_s       */
+    double sustained_s;           /* length of the sustained measurement [s]                    */
+} sdm_device_peaks;
+
+/* Measures the FP64 arithmetic throughput of the current device with chains
+ * of independent fused multiply-adds (2 flops each), on a stream of its own,
+ * timed with CUDA events: the ceiling for the FP64-bound condensation solve
+ * (Sec. 5.1.3).  The paper has no counterpart: a measurement utility.
+ * sustain_s in [0, 60]: length of the back-to-back run (0 skips it).  It
+ * allocates a few KB of device memory and frees it, and synchronises its own
+ * stream.  SDM_EINVAL for bad arguments, SDM_ECUDA if a CUDA call fails
+ * (message in sdm_last_error(NULL)). */
+sdm_status sdm_probe_device(double sustain_s, sdm_device_peaks *out);
+
 /* Counters (completes the stream first). */
 sdm_status sdm_get_stats(sdm_ctx *ctx, sdm_stats *out);
 

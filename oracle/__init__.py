@@ -18,24 +18,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _SRC = [os.path.join(_HERE, f) for f in ("sdm_oracle.c", "philox.c")]
 _lock = threading.Lock()
-_lib = None
+_libs: dict = {}
 
 MAX_MODES = 8
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2)."""
-    os.makedirs(_BUILD, exist_ok=True)
+def _build_one(so: str, extra: list, force: bool) -> str:
     newest = max(os.path.getmtime(p) for p in _SRC + [os.path.join(_HERE, "sdm_oracle.h")])
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= newest:
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] + extra + ["-o", tmp] + _SRC + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def build(force: bool = False, omp: bool | None = None) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2,
+    serial) and its cell-parallel timing build ``liboracle_omp.so`` (the
+    same source with -fopenmp).  ``omp`` None builds both and returns the
+    serial one's path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if omp is None:
+        _build_one(_SO_OMP, ["-fopenmp"], force)
+        return _build_one(_SO, [], force)
+    return _build_one(_SO_OMP, ["-fopenmp"], force) if omp else _build_one(_SO, [], force)
 
 
 class Mode(C.Structure):
@@ -91,11 +102,12 @@ _P = C.POINTER
 _D = C.c_double
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The serial oracle (default) or its cell-parallel OpenMP build."""
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if omp not in _libs:
+            L = C.CDLL(build(omp=omp))
+            L.orc_threads.argtypes = [C.c_int]; L.orc_threads.restype = C.c_int
             L.orc_philox4x64_10.argtypes = [_P(C.c_uint64), _P(C.c_uint64), _P(C.c_uint64)]
             L.orc_u01.argtypes = [C.c_uint64]; L.orc_u01.restype = _D
             L.orc_n_cells.argtypes = [_P(Domain)]; L.orc_n_cells.restype = C.c_int64
@@ -128,8 +140,13 @@ def lib():
             L.orc_sd_conc.argtypes = [_P(Domain), _P(SDs), _P(_D)]
             L.orc_upwind.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), _P(_D), _P(_D)]
             L.orc_relax.argtypes = [_P(Domain), _P(_D), _P(_D), _D, _D]
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(n: int = 0, omp: bool = True) -> int:
+    """Threads the OpenMP build uses (n > 0 sets them); 1 for the serial one."""
+    return int(lib(omp).orc_threads(int(n)))
 
 
 def _dp(a):
@@ -237,10 +254,10 @@ class Oracle:
     """One simulated domain advanced by the oracle, following the paper's
     calling sequence (Sec. 5.2.2): init, then step_sync / step_async pairs."""
 
-    def __init__(self, cfg: dict):
+    def __init__(self, cfg: dict, omp: bool = False):
         self.cfg = dict(cfg)
         self.dom = make_domain(cfg)
-        L = lib()
+        self._L = L = lib(omp)
         self.n_cells = int(L.orc_n_cells(C.byref(self.dom)))
         self.n_groups = int(L.orc_n_groups(C.byref(self.dom)))
         self.step_index = 0
@@ -249,7 +266,7 @@ class Oracle:
 
     def rd_range(self, group=0):
         lo, hi = _D(), _D()
-        rc = lib().orc_rd_range(C.byref(self.dom), group, C.byref(lo), C.byref(hi))
+        rc = self._L.orc_rd_range(C.byref(self.dom), group, C.byref(lo), C.byref(hi))
         if rc != 0:
             raise RuntimeError(f"orc_rd_range failed ({rc})")
         return lo.value, hi.value
@@ -260,7 +277,7 @@ class Oracle:
         st = State(n)
         s = st.struct()
         nreal = np.zeros(n) if with_nreal else None
-        rc = lib().orc_init_cells_nreal(C.byref(self.dom), _dp(np.ascontiguousarray(th, np.float64).ravel()),
+        rc = self._L.orc_init_cells_nreal(C.byref(self.dom), _dp(np.ascontiguousarray(th, np.float64).ravel()),
                                         _dp(np.ascontiguousarray(rv, np.float64).ravel()),
                                         _dp(np.ascontiguousarray(rhod, np.float64).ravel()), len(cells),
                                         cells.ctypes.data_as(_P(C.c_int64)), C.byref(s), _dp(nreal))
@@ -279,13 +296,13 @@ class Oracle:
     def step_sync(self, opts: dict | None = None):
         o = make_opts(opts)
         s = self.state.struct()
-        lib().orc_step_sync(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
+        self._L.orc_step_sync(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
                             _dp(self.rhod), C.byref(self.stats))
 
     def step_async(self, opts: dict | None = None, rhoCx=None, rhoCy=None, rhoCz=None):
         o = make_opts(opts)
         s = self.state.struct()
-        lib().orc_step_async(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
+        self._L.orc_step_async(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
                              _dp(self.rhod), _dp(rhoCx), _dp(rhoCy), _dp(rhoCz),
                              self.step_index, C.byref(self.stats))
         self.step_index += 1
@@ -293,7 +310,7 @@ class Oracle:
     def moments(self, wet: bool, r_min: float, r_max: float, k: int):
         out = np.zeros(self.n_cells)
         s = self.state.struct()
-        lib().orc_moments(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), r_min, r_max, k, _dp(out))
+        self._L.orc_moments(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), r_min, r_max, k, _dp(out))
         return out
 
     def spectrum(self, wet: bool, edges, k: int):
@@ -302,7 +319,7 @@ class Oracle:
         nb = len(edges) - 1
         out = np.zeros(nb * self.n_cells)
         s = self.state.struct()
-        lib().orc_spectrum(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), _dp(edges), nb, k, _dp(out))
+        self._L.orc_spectrum(C.byref(self.dom), C.byref(s), _dp(self.rhod), int(wet), _dp(edges), nb, k, _dp(out))
         return out.reshape(nb, self.n_cells)
 
     def euler_step(self, rhoCx=None, rhoCy=None, rhoCz=None, th0=None, rv0=None, tau_rlx=300.0, z_rlx=200.0):
@@ -317,7 +334,7 @@ class Oracle:
     def sd_conc(self):
         out = np.zeros(self.n_cells)
         s = self.state.struct()
-        lib().orc_sd_conc(C.byref(self.dom), C.byref(s), _dp(out))
+        self._L.orc_sd_conc(C.byref(self.dom), C.byref(s), _dp(out))
         return out
 
 

@@ -15,12 +15,23 @@
  * Functions whose exact formula the paper only cites (transition-regime
  * factors, ventilation, terminal velocity, viscosity) are parity unpinned
  * except for their limits: see orc_growth() and orc_vterm().
+ *
+ * The same source, compiled with -fopenmp, is the oracle's cell-parallel
+ * timing variant (the paper's OpenMP back-end, Sec. 6): the "omp" pragmas
+ * below split the loops over grid cells (cells are independent within
+ * condensation and coalescence) and over super-droplets (terminal velocity,
+ * advection) between threads.  Each cell keeps its own counters, merged
+ * after the cell, so both builds give the same results bit for bit; without
+ * -fopenmp the pragmas are ignored.
  */
 #include "sdm_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI 3.14159265358979323846
 
@@ -41,6 +52,34 @@ static double rho_stp(void) { return 101325.0 / (R_d * 293.15); }
 
 /* (0,1) open-interval uniform from 64 random bits: 52 bits plus one half. */
 double orc_u01(uint64_t v) { return ((double)(v >> 12) + 0.5) * 0x1p-52; }
+
+/* Threads of the cell-parallel build (n > 0 sets them); 1 in the serial one. */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* add one cell's counters to the run's (one thread at a time) */
+static void stats_merge(orc_stats *st, const orc_stats *c)
+{
+    if (!st) return;
+#ifdef _OPENMP
+#pragma omp critical(orc_stats_merge)
+#endif
+    {
+        st->n_pairs += c->n_pairs; st->n_coll += c->n_coll; st->n_pgt1 += c->n_pgt1;
+        st->n_recycled += c->n_recycled; st->n_euler += c->n_euler; st->n_bisect += c->n_bisect;
+        if (c->max_p > st->max_p) st->max_p = c->max_p;
+        st->rainfall += c->rainfall;
+        st->n_coal_substeps += c->n_coal_substeps;
+    }
+}
 
 static void draw(uint64_t seed, uint64_t uid, uint64_t substep, uint64_t step, uint64_t stream,
                  uint64_t out[4])
@@ -415,6 +454,7 @@ static members build_members(const orc_domain *d, const orc_sds *s)
     memcpy(fill, m.start, (size_t)nc * sizeof(int64_t));
     for (int64_t i = 0; i < s->n; ++i) m.idx[fill[cell[i]]++] = i;
     g_uid_for_sort = s->uid;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t c = 0; c < nc; ++c)
         qsort(m.idx + m.start[c], (size_t)(m.start[c + 1] - m.start[c]), sizeof(int64_t),
               cmp_idx_by_uid);
@@ -439,7 +479,10 @@ void orc_condense(const orc_domain *d, const orc_opts *o, orc_sds *s, double *th
     int64_t nc = orc_n_cells(d);
     double dV = cell_volume(d);
     double dtp = d->dt / o->sstp_cond;
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < nc; ++c) {
+        orc_stats cs;
+        memset(&cs, 0, sizeof cs);
         for (int sub = 0; sub < o->sstp_cond; ++sub) {
             orc_thermo t;
             orc_thermo_eval(th[c], rv[c], rhod[c], o->RH_max, &t);
@@ -448,7 +491,7 @@ void orc_condense(const orc_domain *d, const orc_opts *o, orc_sds *s, double *th
                 int64_t i = m.idx[q];
                 if (s->N[i] == 0) continue;
                 double x0 = s->rw2[i];
-                double x1 = orc_solve_rw2(x0, s->rd3[i], s->kappa[i], &t, dtp, d->physics, st);
+                double x1 = orc_solve_rw2(x0, s->rd3[i], s->kappa[i], &t, dtp, d->physics, &cs);
                 s->rw2[i] = x1;
                 sum += (double)s->N[i] * (x1 * sqrt(x1) - x0 * sqrt(x0));
             }
@@ -456,6 +499,7 @@ void orc_condense(const orc_domain *d, const orc_opts *o, orc_sds *s, double *th
             rv[c] = t.rv + drv;
             th[c] = t.th + drv * t.dth_drv;
         }
+        stats_merge(st, &cs);
     }
     free_members(&m);
 }
@@ -559,6 +603,7 @@ void orc_advect(const orc_domain *d, orc_sds *s, const double *rhod, const doubl
                 const double *rhoCy, const double *rhoCz)
 {
     int64_t NY = dimn(d->ny), NZ = dimn(d->nz);
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < s->n; ++q) {
         int64_t c = orc_cell_of(d, s->x[q], s->y[q], s->z[q]);
         int64_t i = c / (NY * NZ), j = (c / NZ) % NY, k = c % NZ;
@@ -591,6 +636,7 @@ void orc_transport(const orc_domain *d, const orc_opts *o, orc_sds *s, const dou
     double *vt = NULL;
     if (o->sedi && d->nz > 0) {
         vt = malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < s->n; ++q) {
             int64_t c = orc_cell_of(d, s->x[q], s->y[q], s->z[q]);
             orc_thermo t;
@@ -753,13 +799,18 @@ void orc_coalesce(const orc_domain *d, const orc_opts *o, orc_sds *s, const doub
     members m = build_members(d, s);
     int64_t nc = orc_n_cells(d);
     double dV = cell_volume(d);
-    shuf *buf = malloc(sizeof(shuf) * (size_t)(s->n > 0 ? s->n : 1));
+    shuf *all = malloc(sizeof(shuf) * (size_t)(s->n > 0 ? s->n : 1));
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < nc; ++c) {
+        shuf *buf = all + m.start[c];  /* room for the cell's members */
+        orc_stats cs;
+        memset(&cs, 0, sizeof cs);
+        orc_stats *cst = st ? &cs : NULL;
         orc_thermo t;
         orc_thermo_eval(th[c], rv[c], rhod[c], 44.0, &t);
         int sstp = o->coal_adapt > 0 ? adaptive_substeps(d, o, &t, s, &m, c, dV) : o->sstp_coal;
         double dtpp = d->dt / sstp;
-        if (st) st->n_coal_substeps += (uint64_t)sstp;
+        if (cst) cst->n_coal_substeps += (uint64_t)sstp;
         for (int sub = 0; sub < sstp; ++sub) {
             int64_t n = 0;
             for (int64_t q = m.start[c]; q < m.start[c + 1]; ++q) {
@@ -779,20 +830,21 @@ void orc_coalesce(const orc_domain *d, const orc_opts *o, orc_sds *s, const doub
                 uint64_t Nmax = s->N[a] > s->N[b] ? s->N[a] : s->N[b];
                 uint64_t Nmin = s->N[a] > s->N[b] ? s->N[b] : s->N[a];
                 double P = (double)Nmax * K * dtpp / dV * scale;
-                if (st) {
-                    st->n_pairs++;
-                    if (P > 1.0) st->n_pgt1++;
-                    if (P > st->max_p) st->max_p = P;
+                if (cst) {
+                    cst->n_pairs++;
+                    if (P > 1.0) cst->n_pgt1++;
+                    if (P > cst->max_p) cst->max_p = P;
                 }
                 uint64_t gamma = n_events(P, orc_u01(buf[2 * k].acc), Nmax, Nmin, o->coal_multi);
                 if (gamma > 0) {
                     collide(s, a, b, gamma);
-                    if (st) st->n_coll++;
+                    if (cst) cst->n_coll++;
                 }
             }
         }
+        stats_merge(st, &cs);
     }
-    free(buf);
+    free(all);
     free_members(&m);
 }
 

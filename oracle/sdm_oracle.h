@@ -70,6 +70,7 @@ typedef struct {
 
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 double orc_u01(uint64_t v);
+int orc_threads(int n);  /* threads of the -fopenmp build (n > 0 sets them); 1 otherwise */
 
 int64_t orc_n_cells(const orc_domain *d);
 int orc_n_groups(const orc_domain *d);

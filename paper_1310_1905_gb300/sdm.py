@@ -88,7 +88,15 @@ SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_st
            "sdm_euler_step",
            "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
-           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc"]
+           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc", "sdm_probe_device"]
+
+
+class sdm_device_peaks(C.Structure):
+    _fields_ = [("n_sm", C.c_int), ("blocks", C.c_int), ("fp64_tflops_burst", C.c_double),
+                ("fp64_tflops_sustained", C.c_double), ("sustained_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def lib_path() -> str:
@@ -130,6 +138,7 @@ def load(build_if_missing: bool = True):
     L.sdm_get_timing.argtypes = [ctx, P(sdm_timing), C.c_int]
     L.sdm_cell_sort.argtypes = [V, I64, C.c_int32, V, V, V]
     L.sdm_cell_sort_noalloc.argtypes = [V, I64, C.c_int32, V, V, V]
+    L.sdm_probe_device.argtypes = [D, P(sdm_device_peaks)]
     for s in SYMBOLS:
         if s != "sdm_last_error":
             getattr(L, s).restype = C.c_int
@@ -373,6 +382,17 @@ def sdm_cell_sort_noalloc(cell, n_cells: int, perm, offsets, stream=None):
     if st != 0:
         msg = L.sdm_last_error(None)
         raise SdmError(st, msg.decode() if msg else "")
+
+
+def sdm_probe_device(sustain_s: float = 2.0) -> dict:
+    """SM count and measured FP64 FMA throughput of the current device."""
+    L = load()
+    out = sdm_device_peaks()
+    st = L.sdm_probe_device(float(sustain_s), C.byref(out))
+    if st != 0:
+        msg = L.sdm_last_error(None)
+        raise SdmError(st, msg.decode() if msg else "sdm_probe_device failed")
+    return out.as_dict()
 
 
 # ---------------------------------------------------------------- object wrapper
