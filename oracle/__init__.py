@@ -119,6 +119,8 @@ def lib(omp: bool = False):
             L.orc_growth.argtypes = [_D, _D, _D, _P(Thermo), C.c_int]; L.orc_growth.restype = _D
             L.orc_solve_rw2.argtypes = [_D, _D, _D, _P(Thermo), _D, C.c_int, _P(Stats)]
             L.orc_solve_rw2.restype = _D
+            L.orc_solve_batch.argtypes = [C.c_int64, _P(_D), _P(_D), _P(_D), _P(C.c_int64), _P(_D), _P(_D),
+                                          _P(_D), _D, _D, C.c_int, _P(_D)]
             L.orc_equilibrium_rw2.argtypes = [_D, _D, _D, _D]; L.orc_equilibrium_rw2.restype = _D
             L.orc_rd_range.argtypes = [_P(Domain), C.c_int, _P(_D), _P(_D)]; L.orc_rd_range.restype = C.c_int
             L.orc_init_cells.argtypes = [_P(Domain), _P(_D), _P(_D), _P(_D), C.c_int64, _P(C.c_int64), _P(SDs)]
@@ -135,6 +137,8 @@ def lib(omp: bool = False):
             L.orc_step_sync.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), _P(Stats)]
             L.orc_step_async.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D),
                                          _P(_D), _P(_D), _P(_D), C.c_uint64, _P(Stats)]
+            L.orc_parcel_step.argtypes = [_P(Domain), _P(Opts), _P(SDs), _P(_D), _P(_D), _P(_D), _D, _D,
+                                          C.c_uint64, _P(Stats)]
             L.orc_moments.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _D, _D, C.c_int, _P(_D)]
             L.orc_spectrum.argtypes = [_P(Domain), _P(SDs), _P(_D), C.c_int, _P(_D), C.c_int, C.c_int, _P(_D)]
             L.orc_sd_conc.argtypes = [_P(Domain), _P(SDs), _P(_D)]
@@ -291,6 +295,8 @@ class Oracle:
         self.rhod = np.array(rhod, np.float64).ravel().copy()
         self.state, self.nreal = self.init_cells(self.th, self.rv, self.rhod, np.arange(self.n_cells),
                                                  with_nreal=True)
+        # dry-air mass of a parcel (no spatial dimension), kept through rho_d changes
+        self.m_d = float(self.rhod[0]) * (self.dom.dx * self.dom.dy * self.dom.dz)
         return self.state
 
     def step_sync(self, opts: dict | None = None):
@@ -306,6 +312,21 @@ class Oracle:
                              _dp(self.rhod), _dp(rhoCx), _dp(rhoCy), _dp(rhoCz),
                              self.step_index, C.byref(self.stats))
         self.step_index += 1
+
+    def parcel_step(self, opts: dict | None = None, rhod: float | None = None):
+        """One timestep of a parcel or box (no spatial dimension): a new
+        rho_d (if given) sets the volume to the dry-air mass over it, then
+        recycling, condensation and coalescence."""
+        o = make_opts(opts)
+        s = self.state.struct()
+        self._L.orc_parcel_step(C.byref(self.dom), C.byref(o), C.byref(s), _dp(self.th), _dp(self.rv),
+                                _dp(self.rhod), self.m_d, float(rhod) if rhod else 0.0, self.step_index,
+                                C.byref(self.stats))
+        self.step_index += 1
+
+    @property
+    def volume(self) -> float:
+        return self.dom.dx * self.dom.dy * self.dom.dz
 
     def moments(self, wet: bool, r_min: float, r_max: float, k: int):
         out = np.zeros(self.n_cells)
@@ -379,3 +400,15 @@ def reynolds(rw2, t: Thermo):
 
 def equilibrium_rw2(rd3, kappa, RH, T):
     return lib().orc_equilibrium_rw2(rd3, kappa, RH, T)
+
+
+def solve_batch(x0, rd3, kappa, cell, th, rv, rhod, dtp, RH_max=44.0, physics=1, omp=True):
+    """x1 of one condensation substep for each listed super-droplet in its
+    cell's state (no feedback): the oracle's bisection, solve by solve."""
+    x0, rd3, kappa = (np.ascontiguousarray(a, np.float64) for a in (x0, rd3, kappa))
+    cell = np.ascontiguousarray(cell, np.int64)
+    th, rv, rhod = (np.ascontiguousarray(a, np.float64).ravel() for a in (th, rv, rhod))
+    out = np.empty_like(x0)
+    lib(omp).orc_solve_batch(len(x0), _dp(x0), _dp(rd3), _dp(kappa), cell.ctypes.data_as(_P(C.c_int64)),
+                             _dp(th), _dp(rv), _dp(rhod), RH_max, dtp, physics, _dp(out))
+    return out

@@ -265,6 +265,23 @@ double orc_solve_rw2(double x0, double rd3, double kappa, const orc_thermo *t, d
     return 0.5 * (lo + hi);
 }
 
+/* One condensation substep's solves for listed super-droplets, each in its
+ * cell's ambient state at (th, rv, rhod), with no feedback on the cell:
+ * x1[q] = orc_solve_rw2(x0[q], ...).  A test driver for comparing solvers
+ * solve by solve along an oracle trajectory. */
+void orc_solve_batch(int64_t n, const double *x0, const double *rd3, const double *kappa,
+                     const int64_t *cell, const double *th, const double *rv, const double *rhod,
+                     double RH_max, double dtp, int physics, double *x1)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        orc_thermo t;
+        int64_t c = cell[q];
+        orc_thermo_eval(th[c], rv[c], rhod[c], RH_max, &t);
+        x1[q] = orc_solve_rw2(x0[q], rd3[q], kappa[q], &t, dtp, physics, NULL);
+    }
+}
+
 /* Wet radius in equilibrium with relative humidity RH: zero left-hand side of
  * eq. (maxmason), i.e. a_w exp(A/r) = RH (Sec. 5.1.6), found by bisection in
  * x = r^2 on [r_d^2, x_hi], where a_w(x_hi) = RH so that the Kelvin factor
@@ -863,6 +880,34 @@ void orc_step_async(const orc_domain *d, const orc_opts *o, orc_sds *s, const do
     if (o->adve || o->sedi)
         orc_transport(d, o, s, th, rv, rhod, o->adve ? rhoCx : NULL, o->adve ? rhoCy : NULL,
                       o->adve ? rhoCz : NULL, st);
+    if (o->coal) orc_coalesce(d, o, s, th, rv, rhod, step, st);
+}
+
+/* ---- parcel framework (Sec. 5.2.1: nx = ny = nz = 0, one cell) ------------
+ * An adiabatic parcel (or a box, when rho_d never changes) advanced one
+ * timestep.  READINGS:
+ *  - the parcel keeps its dry-air mass m_d = rho_d dV: a new rho_d given for
+ *    the step (step_sync's optional rho_d, "needs to be specified only if the
+ *    Eulerian framework allows the density to vary in time") sets
+ *    dV = m_d / rho_d before the step; a value equal to the current one
+ *    changes nothing.  theta (the dry potential temperature) and r_v are
+ *    carried over: T and p follow from them and the new rho_d (Appendix A);
+ *  - the step begins with the recycling of zero-multiplicity super-droplets
+ *    ("at the beginning of each timestep", Sec. 5.1.4), then condensation
+ *    (step_sync), then coalescence; there is no transport.
+ * The volume is kept as dx with dy = dz = 1, so that dx dy dz is m_d / rho_d
+ * exactly. */
+void orc_parcel_step(orc_domain *d, const orc_opts *o, orc_sds *s, double *th, double *rv, double *rhod,
+                     double m_d, double rhod_new, uint64_t step, orc_stats *st)
+{
+    if (rhod_new > 0.0 && rhod_new != rhod[0]) {
+        rhod[0] = rhod_new;
+        d->dx = m_d / rhod_new;
+        d->dy = 1.0;
+        d->dz = 1.0;
+    }
+    orc_recycle(s, st);
+    if (o->cond) orc_condense(d, o, s, th, rv, rhod, st);
     if (o->coal) orc_coalesce(d, o, s, th, rv, rhod, step, st);
 }
 

@@ -82,6 +82,9 @@ double orc_vterm(double rw2, const orc_thermo *t);
 double orc_growth(double x, double rd3, double kappa, const orc_thermo *t, int physics);
 double orc_solve_rw2(double x0, double rd3, double kappa, const orc_thermo *t, double dtp,
                      int physics, orc_stats *st);
+void orc_solve_batch(int64_t n, const double *x0, const double *rd3, const double *kappa,
+                     const int64_t *cell, const double *th, const double *rv, const double *rhod,
+                     double RH_max, double dtp, int physics, double *x1);
 double orc_equilibrium_rw2(double rd3, double kappa, double RH, double T);
 
 int orc_rd_range(const orc_domain *d, int group, double *lnr_min, double *lnr_max);
@@ -106,6 +109,8 @@ void orc_step_sync(const orc_domain *d, const orc_opts *o, orc_sds *s, double *t
 void orc_step_async(const orc_domain *d, const orc_opts *o, orc_sds *s, const double *th,
                     const double *rv, const double *rhod, const double *rhoCx,
                     const double *rhoCy, const double *rhoCz, uint64_t step, orc_stats *st);
+void orc_parcel_step(orc_domain *d, const orc_opts *o, orc_sds *s, double *th, double *rv, double *rhod,
+                     double m_d, double rhod_new, uint64_t step, orc_stats *st);
 void orc_moments(const orc_domain *d, const orc_sds *s, const double *rhod, int wet,
                  double r_min, double r_max, int k, double *out);
 void orc_sd_conc(const orc_domain *d, const orc_sds *s, double *out);
