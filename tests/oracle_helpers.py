@@ -68,3 +68,22 @@ def recycle(state):
     s = state.struct()
     oracle.lib().orc_recycle(C.byref(s), C.byref(st))
     return st
+
+
+def golovin_run(arg):
+    """One seed of the Golovin box (Shima et al. 2009 set-up) in the oracle:
+    (N, r_w^2) at each listed time.  arg = (seed, times, coal_multi); a
+    top-level function so that a spawn-started process pool can run seeds
+    side by side."""
+    import workloads
+    seed, times, multi = arg
+    w = workloads.golovin_box(seed=seed)
+    o = oracle.Oracle(w.cfg)
+    o.init(w.th, w.rv, w.rhod)
+    opts = dict(w.opts, coal_multi=multi)
+    out = {}
+    for t in range(1, max(times) + 1):
+        o.step_async(opts)
+        if t in times:
+            out[t] = (o.state.N.astype(float).copy(), o.state.rw2.copy(), o.stats.n_pgt1)
+    return out

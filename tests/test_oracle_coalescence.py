@@ -160,47 +160,83 @@ def golovin_mass_density(r, t):
     return 3.0 * V * V * n * 1000.0
 
 
+SEEDS = 16
+
+
+def _golovin(times, multi):
+    import multiprocessing as mp
+    import os
+    from oracle_helpers import golovin_run
+    oracle.build()  # before the pool: its workers only load the library
+    args = [(seed, tuple(times), multi) for seed in range(SEEDS)]
+    with mp.get_context("spawn").Pool(min(SEEDS, os.cpu_count() or 1)) as pool:
+        return pool.map(golovin_run, args)
+
+
 @pytest.fixture(scope="module")
 def golovin_runs():
-    snaps = []
-    for seed in range(4):
-        w = workloads.golovin_box(seed=seed)
-        o = oracle.Oracle(w.cfg)
-        o.init(w.th, w.rv, w.rhod)
-        out = {}
-        for t in range(1, 1801):
-            o.step_async(w.opts)
-            if t % 600 == 0:
-                out[t] = (o.state.N.astype(float).copy(), o.state.rw2.copy())
-        snaps.append(out)
-    return snaps
+    """16 seeds of the paper's scheme (one event per pair), to 2400 s."""
+    return _golovin((600, 1200, 1800, 2400), 0)
 
 
-def test_golovin_number_moment(golovin_runs):
-    for t in (600, 1200, 1800):
-        m0 = np.mean([r[t][0].sum() / DV for r in golovin_runs])
-        assert m0 == pytest.approx(N0 * math.exp(-B * N0 * VBAR * t), rel=0.04)
+@pytest.fixture(scope="module")
+def golovin_runs_multi():
+    """16 seeds to 3600 s with multiple coalescence, the treatment of P > 1
+    the paper plans (Sec. 5.1.4): after about 3000 s pairs of mm drops reach
+    P up to 2, and the one-event scheme then undersamples their collisions
+    (its number concentration ends 3 % above the analytic one at 3600 s)."""
+    return _golovin((3600,), 1)
 
 
-def test_golovin_mass_density(golovin_runs):
+def _sem(v):
+    return np.std(v, ddof=1) / math.sqrt(len(v))
+
+
+def test_golovin_number_moment(golovin_runs, golovin_runs_multi):
+    """Mean over 16 seeds of the number concentration against
+    n0 exp(-b n0 Vbar t), within 1 % plus three standard errors."""
+    for runs, times, slack in ((golovin_runs, (600, 1200, 1800, 2400), 0.01), (golovin_runs_multi, (3600,), 0.03)):
+        for t in times:
+            m0 = np.array([r[t][0].sum() / DV for r in runs])
+            ana = N0 * math.exp(-B * N0 * VBAR * t)
+            assert abs(m0.mean() - ana) <= slack * ana + 3.0 * _sem(m0), t
+    # the paper's scheme is what ran to 2400 s: no pair's P exceeded one before 1800 s
+    assert all(r[1800][2] == 0 for r in golovin_runs)
+
+
+def _mass_density_check(runs, t, mean_rel):
     edges = np.linspace(math.log(10e-6), math.log(5e-3), 33)
     mid = np.exp(0.5 * (edges[1:] + edges[:-1]))
-    for t in (1200, 1800):
-        hs = []
-        for r in golovin_runs:
-            N, rw2 = r[t]
-            rr = np.sqrt(rw2)
-            mass = N * 4.0 / 3.0 * math.pi * rr ** 3 * 1000.0 / DV
-            h, _ = np.histogram(np.log(rr), edges, weights=mass)
-            hs.append(h / np.diff(edges))
-        g = golovin_mass_density(mid, t)
-        sel = g > 0.1 * g.max()
-        hs = np.array(hs)
-        sem = hs.std(axis=0, ddof=1)[sel] / math.sqrt(len(hs))  # seed-to-seed error
-        dev = np.abs(hs.mean(axis=0)[sel] - g[sel])
-        assert sel.sum() >= 8
-        assert (dev <= 0.1 * g[sel] + 3.0 * sem).all()
-        assert (dev / g[sel]).mean() < 0.08
-    # total liquid water is conserved: n0 * Vbar * rho_w = 1 g m^-3
-    N, rw2 = golovin_runs[0][1800]
-    assert (N * 4.0 / 3.0 * math.pi * rw2 ** 1.5).sum() / DV == pytest.approx(N0 * VBAR, rel=0.03)
+    hs = []
+    for r in runs:
+        N, rw2 = r[t][0], r[t][1]
+        rr = np.sqrt(rw2)
+        mass = N * 4.0 / 3.0 * math.pi * rr ** 3 * 1000.0 / DV
+        h, _ = np.histogram(np.log(rr), edges, weights=mass)
+        hs.append(h / np.diff(edges))
+    g = golovin_mass_density(mid, t)
+    sel = g > 0.1 * g.max()
+    hs = np.array(hs)
+    sem = hs.std(axis=0, ddof=1)[sel] / math.sqrt(len(hs))  # seed-to-seed error
+    dev = np.abs(hs.mean(axis=0)[sel] - g[sel])
+    assert sel.sum() >= 8
+    assert (dev <= 0.1 * g[sel] + 3.0 * sem).all(), t
+    assert (dev / g[sel]).mean() < mean_rel, t
+
+
+def test_golovin_mass_density(golovin_runs, golovin_runs_multi):
+    """The mass density per unit ln r at 1200, 2400 and 3600 s: every bin
+    holding more than a tenth of the peak within 10 % plus three standard
+    errors of the 16-seed mean, and the mean relative deviation small."""
+    _mass_density_check(golovin_runs, 1200, 0.05)
+    _mass_density_check(golovin_runs, 2400, 0.08)
+    _mass_density_check(golovin_runs_multi, 3600, 0.16)
+    # liquid water: n0 Vbar rho_w = 1 g m^-3 up to the sampling of the initial
+    # volumes, and conserved by the collisions to rounding
+    def vol(runs, t, k=0):
+        N, rw2 = runs[k][t][0], runs[k][t][1]
+        return (N * 4.0 / 3.0 * math.pi * rw2 ** 1.5).sum() / DV
+
+    assert vol(golovin_runs_multi, 3600) == pytest.approx(N0 * VBAR, rel=0.03)
+    for k in range(SEEDS):
+        assert vol(golovin_runs, 2400, k) == pytest.approx(vol(golovin_runs, 600, k), rel=1e-12)

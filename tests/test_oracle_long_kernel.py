@@ -18,10 +18,17 @@ def max_p(kernel, R, r, N=(10 ** 6, 10 ** 6)):
     return coalesce(cfg, s, step=0).max_p
 
 
+def long_cgs(R, r):
+    """Long's (1974) efficiency as he states it, with the radii in cm:
+    E = 4.5e4 R^2 (1 - 3e-4 / r); the oracle writes it in SI units."""
+    Rc, rc = R * 100.0, r * 100.0
+    return 4.5e4 * Rc * Rc * (1.0 - 3e-4 / rc)
+
+
 @pytest.mark.parametrize("R,r,E", [(60e-6, 55e-6, 1.0),                                   # R >= 50 um
                                    (40e-6, 2e-6, 1e-3),                                    # floor
-                                   (20e-6, 10e-6, 4.5e8 * 20e-6 ** 2 * (1 - 3e-6 / 10e-6)),
-                                   (45e-6, 40e-6, 4.5e8 * 45e-6 ** 2 * (1 - 3e-6 / 40e-6)),
+                                   (20e-6, 10e-6, long_cgs(20e-6, 10e-6)),                 # 0.126
+                                   (45e-6, 40e-6, long_cgs(45e-6, 40e-6)),                 # 0.843
                                    (49.5e-6, 45e-6, 1.0)])                                 # formula > 1: cap
 def test_efficiency_is_the_ratio_to_the_geometric_kernel(R, r, E):
     assert 0 < E <= 1
