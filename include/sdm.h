@@ -254,6 +254,14 @@ sdm_status sdm_diag_mom(sdm_ctx *ctx, int k);
  * output buffer. */
 sdm_status sdm_diag_sd_conc(sdm_ctx *ctx);
 
+/* The ambient state per cell that the condensation solve sees (Appendix A:
+ * T and p diagnosed from theta, r_v and rho_d; Sec. 5.1.3: the saturation
+ * vapour density), from the context's current theta, r_v and rho_d, into
+ * the output buffer.  what: 0 = T [K], 1 = p [Pa], 2 = rho_vs [kg m^-3],
+ * 3 = RH = rho_v / rho_vs (not capped by RH_max).  SDM_EINVAL for another
+ * value. */
+sdm_status sdm_diag_ambient(sdm_ctx *ctx, int what);
+
 /* Copy the output buffer (n_cells float64, row-major (x, y, z)) to dst,
  * host (dst_on_device = 0, complete on return) or device memory. */
 sdm_status sdm_outbuf(sdm_ctx *ctx, double *dst, int dst_on_device);
@@ -335,9 +343,11 @@ sdm_status sdm_cell_sort(const uint32_t *cell, int64_t n, int32_t n_cells, uint3
  * about 10 MB, reserved on every GPU that loads the library until the
  * process exits.  Limits: n <= 2097152 particles and n_cells <= 524288
  * cells per call, else SDM_EINVAL (message in sdm_last_error(NULL)).
- * The first call on a device resolves the array's device address on that
- * device (it must be the current device); make that first call before any
- * stream capture.  The work is only enqueued on stream: nothing is
+ * A call outside stream capture resolves the array's device address on the
+ * current device (a cudaDeviceReset may move it); a call inside a capture
+ * uses the address the last uncaptured call on that device resolved, so make
+ * the first call on a device, and the first after a cudaDeviceReset, before
+ * any stream capture.  The work is only enqueued on stream: nothing is
  * synchronised.  All calls share the one array, so calls whose work overlaps
  * on the GPU (other streams, other host threads) race; order them on one
  * stream.  Cell indices out of range are skipped, not written: then

@@ -742,6 +742,28 @@ __device__ __noinline__ Thermo thermo_cond(double th, double rv, double rd, doub
     return thermo_eval_f<true>(th, rv, rd, RH_max, rdf);
 }
 
+// The ambient state the solve sees, per cell, into out: the same out-of-line
+// thermodynamics the condensation kernel calls (what: 0 T, 1 p, 2 rho_vs,
+// 3 RH = rho_v / rho_vs), p = rho_d (R_d + r_v R_v) T (Appendix A).
+__global__ void k_cond_ambient(const double *th, const double *rv, const double *rhod, int n_cells, int what,
+                               double *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    const Thermo t = thermo_cond(th[c], rv[c], rhod[c], 44.0, rhod_factor(rhod[c]));
+    double v = t.T;
+    if (what == 1) v = rhod[c] * (phys::R_d + rv[c] * phys::R_v) * t.T;
+    else if (what == 2) v = t.rho_vs;
+    else if (what == 3) v = t.rho_v / t.rho_vs;
+    out[c] = v;
+}
+
+cudaError_t launch_cond_ambient(sdm_ctx *c, int what) {
+    const int B = 128;
+    k_cond_ambient<<<grid_for(c->grid.n_cells, B), B, 0, c->stream>>>(c->th, c->rv, c->rhod, c->grid.n_cells, what,
+                                                                       c->outbuf);
+    return cudaGetLastError();
+}
+
 // ORD: the warps take their work in order of decreasing cost (order),
 // which the previous launch recorded per warp into cost (its FP64 growth
 // evaluations, the bulk of a warp's time); see launch_condense_lpc.
@@ -933,8 +955,8 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
     const int tile = blockIdx.x;
     const MemberDev &md = M[tile_member[tile]];
     __shared__ ThermoF s_tf;
-    if (threadIdx.x == 0) {
-        s_t = thermo_eval_f<true>(md.th, md.rv, md.rhod, p.RH_max, rhod_factor(md.rhod));
+    if (threadIdx.x == 0) {  // the single-context kernel's thermodynamics, the same code
+        s_t = thermo_cond(md.th, md.rv, md.rhod, p.RH_max, rhod_factor(md.rhod));
         s_tf = to_float(s_t);
     }
     __syncthreads();

@@ -723,6 +723,15 @@ sdm_status sdm_diag_sd_conc(sdm_ctx *c) {
     return SDM_OK;
 }
 
+sdm_status sdm_diag_ambient(sdm_ctx *c, int what) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (what < 0 || what > 3) return fail(c, SDM_EINVAL, "what must be 0 (T), 1 (p), 2 (rho_vs) or 3 (RH)");
+    Phase ph(c, PH_DIAG);
+    CK(launch_cond_ambient(c, what), "ambient");
+    c->tacc.launches += 1;
+    return SDM_OK;
+}
+
 sdm_status sdm_diag_spectrum(sdm_ctx *c, int wet, const double *edges, int n_bins, int k, double *dst,
                              int dst_on_device) {
     if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");

@@ -370,6 +370,7 @@ cudaError_t launch_recycle_small(sdm_ctx *c);
 cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
 cudaError_t launch_moments(sdm_ctx *c, int k);
 cudaError_t launch_sd_conc(sdm_ctx *c);
+cudaError_t launch_cond_ambient(sdm_ctx *c, int what);
 constexpr int kMaxSpectrumBins = 256;
 // records per tile of the ensemble's radix sort: the histogram table its
 // callers allocate holds 256 counts per tile of this size

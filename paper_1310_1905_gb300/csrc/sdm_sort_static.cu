@@ -24,19 +24,27 @@ std::mutex g_setup_mutex;
 uint32_t *g_scratch_addr[kMaxDevices] = {};
 
 // Host code cannot use g_sort_scratch's name as a device address; resolve
-// it once per device, with that device current.
-cudaError_t scratch_for_current_device(uint32_t **out) {
+// it on the current device.  Outside stream capture every call resolves it
+// afresh (a cudaDeviceReset reloads the module, and the array may then sit
+// elsewhere); inside a capture the address cached by the last such call on
+// this device is used, so the first call on a device must come before any
+// capture.
+cudaError_t scratch_for_current_device(cudaStream_t st, uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sort_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = (uint32_t *)p;
     }
+    if (!g_scratch_addr[dev]) return cudaErrorStreamCaptureUnsupported;
     *out = g_scratch_addr[dev];
     return cudaSuccess;
 }
@@ -57,7 +65,7 @@ extern "C" sdm_status sdm_cell_sort_noalloc(const uint32_t *cell, int64_t n, int
         return SDM_EINVAL;
     }
     uint32_t *scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) {
+    if (scratch_for_current_device((cudaStream_t)stream, &scratch) != cudaSuccess) {
         cudaGetLastError();
         sdm_set_global_error("sdm_cell_sort_noalloc: device scratch is not reachable");
         return SDM_ECUDA;

@@ -86,7 +86,7 @@ class sdm_timing(C.Structure):
 
 SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_step_async", "sdm_wait",
            "sdm_euler_step",
-           "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
+           "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_ambient", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
            "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc", "sdm_probe_device"]
 
@@ -125,6 +125,7 @@ def load(build_if_missing: bool = True):
     L.sdm_diag_rng.argtypes = [ctx, C.c_int, D, D]
     L.sdm_diag_mom.argtypes = [ctx, C.c_int]
     L.sdm_diag_sd_conc.argtypes = [ctx]
+    L.sdm_diag_ambient.argtypes = [ctx, C.c_int]
     L.sdm_outbuf.argtypes = [ctx, V, C.c_int]
     L.sdm_diag_spectrum.argtypes = [ctx, C.c_int, P(C.c_double), C.c_int, C.c_int, V, C.c_int]
     L.sdm_sizes.argtypes = [ctx, P(I64), P(I64)]
@@ -263,6 +264,14 @@ def sdm_diag_rng(ctx, wet: bool, r_min: float, r_max: float):
 def sdm_diag_mom(ctx, k: int):
     L = load()
     _check(L, ctx, L.sdm_diag_mom(ctx, k))
+
+
+AMBIENT = {"T": 0, "p": 1, "rho_vs": 2, "RH": 3}
+
+
+def sdm_diag_ambient(ctx, what: str):
+    L = load()
+    _check(L, ctx, L.sdm_diag_ambient(ctx, AMBIENT[what]))
 
 
 def sdm_diag_sd_conc(ctx):
@@ -422,6 +431,11 @@ class Particles:
         sdm_diag_mom(self.ctx, k)
         return sdm_outbuf(self.ctx)
 
+    def diag_ambient(self, what: str):
+        """T, p, rho_vs or RH per cell, as the condensation solve sees them."""
+        sdm_diag_ambient(self.ctx, what)
+        return sdm_outbuf(self.ctx)
+
     def diag_sd_conc(self):
         sdm_diag_sd_conc(self.ctx)
         return sdm_outbuf(self.ctx)
@@ -431,6 +445,10 @@ class Particles:
 
     def attr(self, name):
         return sdm_get_attr(self.ctx, name)
+
+    def set_attr(self, name, values):
+        """Overwrite one attribute (storage order, as attr() returns it)."""
+        sdm_set_attr(self.ctx, name, values)
 
     def state(self) -> dict:
         """All attributes of present dimensions, ordered by super-droplet id."""

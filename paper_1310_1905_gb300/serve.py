@@ -53,12 +53,13 @@ class Server:
     """Serves requests on one GPU with a fixed device-memory budget."""
 
     def __init__(self, mem_budget_bytes: int, max_members: int = 512, precision: str = "mixed",
-                 opts: dict | None = None, dt: float = 1.0, graph: bool = True):
+                 opts: dict | None = None, dt: float = 1.0, graph: bool = True, keep_state: bool = False):
         self.max_sd = max(1024, int(mem_budget_bytes // BYTES_PER_SD))
         self.ens = Ensemble(dt=dt, precision=precision, max_sd=self.max_sd, max_members=max_members)
         self.max_members = max_members
         self.opts = opts or dict(adve=0, sedi=0, cond=1, coal=1, RH_max=44.0, sstp_cond=10, sstp_coal=10)
         self.graph = graph
+        self.keep_state = keep_state  # copy each finished member's super-droplets into its result
         self.queue: collections.deque[Request] = collections.deque()
         self.resident: list[Request] = []
         self.finished: list[Request] = []
@@ -110,6 +111,9 @@ class Server:
             if r._t >= r.steps:
                 self._retired_last = True
                 r.result = diagnostics(self.ens, r._mid)
+                if self.keep_state:
+                    n = r.member["n_sd"]
+                    r.result["state"] = {k: self.ens.attr(r._mid, k, n) for k in ("N", "rw2", "rd3", "kappa")}
                 self.ens.remove(r._mid)
                 self.resident_sd -= r.member["n_sd"]
                 self.finished.append(r)

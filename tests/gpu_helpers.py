@@ -83,3 +83,19 @@ def compare_states(g, r, rtol=RTOL, exact_N=True, nreal=None):
     for d in ("x", "y", "z"):
         if d in g:
             assert_close(d, g[d], r[d], rtol, atol=1e-9)
+
+
+R_D, R_V, C_PD = 287.0, 461.5, 1005.0
+
+
+def theta_ulps(T_gpu, rho_vs_gpu, th, rv, rhod):
+    """The change of theta, in ulps of theta, that moves the oracle's T and
+    rho_vs as far as they differ from the GPU's (d ln T / d ln theta =
+    c_pd / (c_pd - R_d), d ln rho_vs / d ln T = l_v / (R_v T) - 1): the
+    input perturbation under which the oracle's own spread measures what the
+    two math libraries' rounding of exp, pow and log can move a result."""
+    t = oracle.thermo(th, rv, rhod)
+    dT = abs(T_gpu / t.T - 1.0)
+    drho = abs(rho_vs_gpu / t.rho_vs - 1.0)
+    eth = (C_PD - R_D) / C_PD * max(dT, drho / (t.lv / (R_V * t.T) - 1.0))
+    return max(1, int(np.ceil(eth / (np.spacing(th) / th))))

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import workloads
 from gpu_helpers import RTOL, assert_close, gpu_particles, rounding_ambiguous
+from paper_1310_1905_gb300 import sdm
 
 pytestmark = pytest.mark.gpu
 
@@ -34,22 +35,44 @@ def oracle_cells(w, cells):
     return o, nreal
 
 
-def ulp_spread(w, cells, opts, name="rw2", ulps=4):
-    """How far the oracle's own result moves when theta changes by a few
-    ulps in the sampled cells (after initialisation, before the step): the
-    part of the FP64 answer that its inputs' last bits decide.  The two
-    sides' temperatures and saturation densities differ by about that much
-    (exp and pow round differently in the two math libraries).  Near
+R_D, R_V, C_PD = 287.0, 461.5, 1005.0
+
+
+def measured_theta_ulps(p, o, cells):
+    """Per sampled cell, the theta change (in ulps of theta) that moves the
+    oracle's T and rho_vs as far as they actually differ from the GPU's
+    (measured: sdm_diag_ambient gives the values the condensation kernel
+    computes, from the same theta, r_v, rho_d).  exp, pow and log round
+    differently in the two math libraries; since d ln T / d ln theta =
+    c_pd / (c_pd - R_d) and d ln rho_vs / d ln T = l_v / (R_v T) - 1, a
+    relative difference of T or rho_vs is that of theta times those
+    factors."""
+    Tg, rg = p.diag_ambient("T")[cells], p.diag_ambient("rho_vs")[cells]
+    k = np.ones(len(cells), np.int64)
+    for q, c in enumerate(cells):
+        t = oracle.thermo(o.th[c], o.rv[c], o.rhod[c])
+        dT = abs(Tg[q] / t.T - 1.0)
+        drho = abs(rg[q] / t.rho_vs - 1.0)
+        eth = (C_PD - R_D) / C_PD * max(dT, drho / (t.lv / (R_V * t.T) - 1.0))
+        k[q] = max(1, int(math.ceil(eth / (np.spacing(o.th[c]) / o.th[c]))))
+    return k
+
+
+def ulp_spread(w, cells, opts, ulps, name="rw2"):
+    """How far the oracle's own result moves when theta changes by the
+    given number of ulps per cell (after initialisation, before the step):
+    the part of the FP64 answer that its inputs' last bits decide.  Near
     activation the growth rate is a small difference of nearly equal vapour
-    densities and this spread exceeds 1e-12 for a few droplets."""
+    densities, and this spread exceeds 1e-12 for a few droplets."""
     base, _ = oracle_cells(w, cells)
     base.step_sync(opts)
     ref = getattr(base.state.sorted_by_uid(), name)
     spread = np.zeros_like(ref)
     for direction in (np.inf, -np.inf):
         o, _ = oracle_cells(w, cells)
-        for _ in range(ulps):
-            o.th[cells] = np.nextafter(o.th[cells], direction)
+        for q, c in enumerate(cells):
+            for _ in range(int(ulps[q])):
+                o.th[c] = np.nextafter(o.th[c], direction)
         o.step_sync(opts)
         spread = np.maximum(spread, np.abs(getattr(o.state.sorted_by_uid(), name) - ref))
     return ref, spread
@@ -81,6 +104,8 @@ def test_full_size_sampled_cells(name):
     tie_cells = set((sel[bad] // per_cell).tolist())
     keep = np.array([c for c in cells if c not in tie_cells])
     ksel = (keep[:, None] * per_cell + np.arange(per_cell)[None, :]).ravel()
+    # the measured difference of the two sides' T and rho_vs, as theta ulps
+    ulps = measured_theta_ulps(p, o, keep)
     # condensation (all substeps) on both
     th, rv = np.ascontiguousarray(w.th).copy(), np.ascontiguousarray(w.rv).copy()
     p.step_sync(COND, th, rv)
@@ -90,9 +115,9 @@ def test_full_size_sampled_cells(name):
     _, g = by_uid(p, ["rw2"])
     s = o.state.sorted_by_uid()
     m = np.isin(s.uid.astype(np.int64), ksel)
-    # 1e-12 relative, or the oracle's own spread under a few ulps of theta
-    # where that is wider
-    ref, spread = ulp_spread(w, keep, COND)
+    # 1e-12 relative, or the oracle's own spread under the measured theta
+    # difference where that is wider
+    ref, spread = ulp_spread(w, keep, COND, ulps)
     assert np.array_equal(ref, s.rw2[m])
     wide = spread > RTOL * ref
     assert wide.mean() < 0.05, f"{wide.sum()} of {wide.size} droplets are ill-conditioned"
@@ -101,8 +126,10 @@ def test_full_size_sampled_cells(name):
     tol = np.maximum(RTOL * ref, spread)
     assert (err <= tol).all(), f"rw2 after condensation: {(err > tol).sum()} of {err.size} outside " \
                                f"max(1e-12, spread); worst rel {np.max(err / ref):.3e}"
-    print(f"{name}: {wide.sum()} of {wide.size} droplets wider than 1e-12 under a 4-ulp change of theta; "
-          f"GPU-oracle worst rel {np.max(err / ref):.3e}, worst outside 1e-12 {np.max((err / ref)[~wide]):.3e}")
+    print(f"{name}: theta ulps matching the measured T/rho_vs difference: median {np.median(ulps):.0f}, "
+          f"max {ulps.max()}; {wide.sum()} of {wide.size} droplets wider than 1e-12 under them; "
+          f"GPU-oracle worst rel {np.max(err / ref):.3e}, worst outside 1e-12 {np.max((err / ref)[~wide]):.3e}, "
+          f"{(err > RTOL * ref).sum()} beyond 1e-12")
     # coalescence (all substeps) from the initial state on both
     p2 = gpu_particles(w)
     p2.step_async(COAL)
@@ -180,3 +207,31 @@ def test_full_size_spectrum(name):
         m = cell == c
         ref = np.bincount(b[m], weights=g["N"][m].astype(float) * r[m] ** 3, minlength=64) / (rhod[c] * dV)
         assert_close(f"spectrum of cell {c}", spec[:, c], ref, atol=1e-300)
+
+
+@pytest.mark.parametrize("name,steps", [("icmw_2d", 10), ("updraft_3d", 2)])
+def test_full_domain_fast_solve_is_the_bisection(name, steps):
+    """Every droplet of the full domain: the fast solver (SDM_SOLVER_FAST,
+    the bench's) against the device's own implementation of the paper's
+    bisection (SDM_SOLVER_BISECT, which the small-case tests check against
+    the oracle), from the same state, step after step: both take the same
+    device thermodynamics, so they must agree within 1e-12 everywhere."""
+    w = workload(name)
+    fast = gpu_particles(w)
+    bis = sdm.Particles(dict(w.cfg, cond_solver="bisect"), w.th, w.rv, w.rhod, w.rhoCx, w.rhoCy, w.rhoCz)
+    th, rv = np.ascontiguousarray(w.th).copy(), np.ascontiguousarray(w.rv).copy()
+    worst = 0.0
+    for _ in range(steps):
+        uid = fast.attr("uid")
+        assert np.array_equal(uid, bis.attr("uid"))
+        bis.set_attr("rw2", fast.attr("rw2"))
+        th_b, rv_b = th.copy(), rv.copy()
+        fast.step_sync(COND, th, rv)
+        bis.step_sync(COND, th_b, rv_b)
+        a, b = fast.attr("rw2"), bis.attr("rw2")
+        rel = np.abs(a - b) / b
+        worst = max(worst, rel.max())
+        assert (rel <= RTOL).all(), f"{(rel > RTOL).sum()} of {rel.size} beyond 1e-12, worst {rel.max():.3e}"
+        assert_close("theta", th, th_b)
+        assert_close("r_v", rv, rv_b)
+    print(f"{name}: {w.n_sd} droplets x {steps} steps, worst fast-bisection difference {worst:.3e}")
