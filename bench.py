@@ -91,18 +91,31 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cells", type=int, default=128, help="updraft_3d: cells per dimension")
+    ap.add_argument("--cond-layout", default="auto", choices=["auto", "fused", "staged"],
+                    help="condensation kernels: fused, staged, or chosen by domain size")
+    ap.add_argument("--profile-one-step", action="store_true",
+                    help="ensemble: bracket one graph-replayed step after the warm-up with cudaProfilerStart/Stop "
+                         "(for an ncu kernel list taken with --profile-from-start off)")
+    ap.add_argument("--serve-requests", type=int, default=500, help="serve: requests per window")
+    ap.add_argument("--serve-scale", type=float, default=1.0 / 6.0,
+                    help="serve: factor on the 300-1800 steps of a request")
+    ap.add_argument("--serve-sample", type=int, default=24,
+                    help="serve: requests solved alone to fit the sequential service time")
     ap.add_argument("--diag", action="store_true",
                     help="also run the diagnostics after every step (moments k = 0..3 and a 64-bin spectrum of "
                          "the wet radius), as an output step of a model would; off for the headline number")
     return ap.parse_args()
 
 
-def make_workload(name: str, seed: int, cells: int = 128):
+def make_workload(name: str, seed: int, cells: int = 128, cond_layout: str = "auto"):
     if name == "icmw_2d":
-        return workloads.icmw_2d(seed=seed)
-    if name == "updraft_3d":
-        return workloads.updraft_3d(nx=cells, ny=cells, nz=cells, seed=seed)
-    return workloads.golovin_box(seed=seed)
+        w = workloads.icmw_2d(seed=seed)
+    elif name == "updraft_3d":
+        w = workloads.updraft_3d(nx=cells, ny=cells, nz=cells, seed=seed)
+    else:
+        w = workloads.golovin_box(seed=seed)
+    w.cfg["cond_layout"] = cond_layout
+    return w
 
 
 def workload_desc(w) -> dict:
@@ -174,7 +187,7 @@ def run_gpu(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    w = make_workload(args.workload, seed=rank, cells=args.cells)
+    w = make_workload(args.workload, seed=rank, cells=args.cells, cond_layout=args.cond_layout)
     opts = w.opts
     if args.workload == "golovin_box":
         opts = dict(w.opts)
@@ -295,7 +308,7 @@ def run_ensemble(args, rank: int, world: int) -> dict:
     prec = args.precision if args.precision != "fp64" else "mixed"
     ens = Ensemble(precision=prec, max_sd=n_sd + 1024, max_members=len(members))
     ids = [ens.add(m) for m in members]
-    tile, thr = ens.autotune(opts)
+    tile, thr, pth = ens.autotune(opts)
     ens.use_graph(True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     t = [0.0]
@@ -310,6 +323,12 @@ def run_ensemble(args, rank: int, world: int) -> dict:
         step(ens, idmap)
         t[0] += 1.0
     torch.cuda.synchronize()
+    if args.profile_one_step:
+        torch.cuda.cudart().cudaProfilerStart()
+        step(ens, idmap)
+        t[0] += 1.0
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
     dist_barrier(world)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
@@ -340,44 +359,90 @@ def run_ensemble(args, rank: int, world: int) -> dict:
     t_seq = time.perf_counter() - t0
     for e, _ in solo:
         e.close()
-    return dict(t=dist_max(t_tot, world), n_sd=n_sd, steps=args.steps, clocks=clk, tile=(tile, thr),
+    return dict(t=dist_max(t_tot, world), n_sd=n_sd, steps=args.steps, clocks=clk, tile=(tile, thr, pth),
                 seq_value=n_sd * seq_steps / t_seq, stats=stats, precision=prec, members=len(members))
 
 
 def run_serve(args, rank: int) -> dict:
     """Served stream: Poisson arrivals of parcel/box requests, N_sd
-    log-uniform in [1e3, 2e6], w in [0.1, 5] m/s, mixed precision.  A fixed
-    window of requests with the step counts of the served workload scaled by
-    1/10 (30-180 steps) so that a run takes seconds; served at the offered
-    rate (200 req/s, above capacity) and at half the measured capacity."""
+    log-uniform in [1e3, 2e6], w in [0.1, 5] m/s, mixed precision, 500
+    requests per window (--serve-requests), step counts 300-1800 scaled by
+    --serve-scale (1/6 by default: 50-300 steps, so that a window takes a
+    few minutes), served at the offered rate (200 req/s, above capacity)
+    and at half the measured capacity.  Beside it, the same requests as
+    sequential plain solves: a sample of them solved one by one, each alone
+    on the GPU, gives the service time t = a steps + b n_sd steps, and a
+    first-come-first-served single server on the same arrival times gives
+    their latencies."""
     import torch
 
+    from paper_1310_1905_gb300.ensemble import Ensemble
     from paper_1310_1905_gb300.serve import Server, poisson_requests
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     free, _ = torch.cuda.mem_get_info()
     budget = int(free * 0.5)
+    prec = args.precision if args.precision != "fp64" else "mixed"
+    opts = dict(adve=0, sedi=0, cond=1, coal=1, RH_max=44.0, sstp_cond=10, sstp_coal=10)
 
     def rhod_fn(m, t):
         return float(workloads.hydrostatic_rhod(np.array([m["z0"] + m["w"] * t]), 289.0, 7.5e-3, 101500.0)[0])
 
-    n_req = max(8, args.steps * 2)
+    n_req = args.serve_requests
+    lo, hi = max(1, round(300 * args.serve_scale)), max(1, round(1800 * args.serve_scale))
     members = workloads.ensemble_members(n_req, seed=100 + rank, n_min=1e3, n_max=2e6, parcel_fraction=0.8)
-    out = {}
+    out, arrivals = {}, {}
     cap = None
     for label, rate in (("offered_200_per_s", 200.0), ("half_capacity", None)):
         if rate is None:
-            mean_work = np.mean([m["n_sd"] for m in members]) * 105.0
+            mean_work = np.mean([m["n_sd"] for m in members]) * 0.5 * (lo + hi)
             rate = 0.5 * cap / mean_work
-        reqs = poisson_requests(members, rate, (30, 180), seed=7, rhod_fn=rhod_fn)
-        srv = Server(mem_budget_bytes=budget, precision=args.precision if args.precision != "fp64" else "mixed")
+        reqs = poisson_requests(members, rate, (lo, hi), seed=7, rhod_fn=rhod_fn)
+        arrivals[label] = [(r.arrival, r.member["n_sd"], r.steps) for r in reqs]
+        srv = Server(mem_budget_bytes=budget, precision=prec, opts=opts)
         st = srv.run(reqs)
         srv.close()
         st["rate_per_s"] = rate
         out[label] = st
         if cap is None:
             cap = st["sd_steps_per_s"]
-    return dict(out=out, n_req=n_req, budget=budget)
+    # sequential plain solves: service times of a sample, each request alone
+    rng = np.random.default_rng(3)
+    reqs = poisson_requests(members, 200.0, (lo, hi), seed=7, rhod_fn=rhod_fn)
+    order = np.argsort([r.member["n_sd"] for r in reqs])
+    sample = [reqs[int(i)] for i in order[np.linspace(0, len(order) - 1, args.serve_sample).astype(int)]]
+    rows = []
+    for k, r in enumerate([sample[0]] + sample):  # the first, untimed: module loading and graph capture
+        e = Ensemble(precision=prec, max_sd=r.member["n_sd"], max_members=1)
+        mid = e.add(r.member)
+        e.use_graph(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(r.steps):
+            e.step(opts, rhod={mid: r.rhod_of_t(k + 1.0)} if r.rhod_of_t else None)
+            e.wait()
+        if k > 0:
+            rows.append((r.steps, r.member["n_sd"] * r.steps, time.perf_counter() - t0))
+        e.close()
+    # t = a steps + b SD-steps, least squares in relative error (rows / t)
+    A = np.array([[s_, w_] for s_, w_, _ in rows], float)
+    tt = np.array([t for *_, t in rows])
+    coef, *_ = np.linalg.lstsq(A / tt[:, None], np.ones_like(tt), rcond=None)
+    rel = np.abs(A @ coef - tt) / tt
+    fit_err = dict(median=float(np.median(rel)), worst=float(rel.max()))
+    seq = {}
+    for label, arr in arrivals.items():
+        t_free, lat, work = 0.0, [], 0.0
+        for t_arr, n_sd, steps in arr:
+            start = max(t_arr, t_free)
+            t_free = start + coef[0] * steps + coef[1] * n_sd * steps
+            lat.append(t_free - t_arr)
+            work += n_sd * steps
+        seq[label] = dict(p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
+                          sd_steps_per_s=work / t_free)
+    return dict(out=out, n_req=n_req, budget=budget, steps=(lo, hi), seq=seq, precision=prec,
+                seq_model=dict(a_s_per_step=float(coef[0]), b_s_per_sd_step=float(coef[1]), samples=len(rows),
+                               fit_rel_err=fit_err))
 
 
 def dist_barrier(world):
@@ -530,16 +595,25 @@ def main():
         r = run_serve(args, rank)
         if rank == 0:
             sat = r["out"]["offered_200_per_s"]
-            line = dict(metric=METRIC, value=sat["sd_steps_per_s"], unit=UNIT, n_gpus=world, steps=args.steps,
+            lo, hi = r["steps"]
+            line = dict(metric=METRIC, value=sat["sd_steps_per_s"], unit=UNIT, n_gpus=world, steps=sat["steps"],
                         warmup=0, ms_per_step=sat["wall_s"] / max(1, sat["steps"]) * 1e3, higher_is_better=True,
                         scaling="weak", vs_baseline=None, dtype="f64/f32", data="synthetic",
-                        config=dict(workload=f"served stream: {r['n_req']} Poisson requests, parcel/box, N_sd "
-                                             f"log-uniform in [1e3, 2e6], 30-180 steps, mixed precision, "
-                                             f"arena {r['budget'] / 1e9:.1f} GB"),
+                        config=dict(workload=f"served stream: {r['n_req']} Poisson requests per window, parcels "
+                                             f"(80 %, w in [0.1, 5] m/s) and boxes, N_sd log-uniform in "
+                                             f"[1e3, 2e6], {lo}-{hi} steps (300-1800 x {args.serve_scale:.4g}), "
+                                             f"{r['precision']} precision, arena of {sat['arena_sd']} SDs "
+                                             f"({sat['arena_bytes'] / 1e9:.1f} GB reserved, "
+                                             f"{sat['bytes_per_sd']:.1f} B/SD)"),
                         latency={k: dict(p50_s=v["p50_latency_s"], p99_s=v["p99_latency_s"],
                                          rate_per_s=v["rate_per_s"], sd_steps_per_s=v["sd_steps_per_s"],
-                                         mean_queue_wait_s=v["mean_queue_wait_s"], served=v["served"])
+                                         mean_queue_wait_s=v["mean_queue_wait_s"], served=v["served"],
+                                         peak_resident_sd=v["peak_resident_sd"], wall_s=v["wall_s"])
                                  for k, v in r["out"].items()},
+                        sequential=dict(latency=r["seq"], model=r["seq_model"],
+                                        how="each sampled request solved alone (one-member graph-replayed "
+                                            "ensemble, its own steps), t = a steps + b SD-steps fitted, then a "
+                                            "first-come-first-served single server on the same arrivals"),
                         timing="host wall clock over the whole window")
             print(json.dumps(line), flush=True)
         return

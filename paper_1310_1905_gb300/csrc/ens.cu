@@ -84,6 +84,7 @@ struct sdm_ens {
     bool use_graph = false;
     // tuning: tile size and threads per block of the condensation launch
     int tile = 256, cond_threads = 128, pair_threads = 256;
+    size_t reserved = 0;  // device bytes the arena holds from creation to destruction
     std::string err;
 };
 
@@ -594,6 +595,33 @@ sdm_status repack(sdm_ens *e, std::vector<MemberInitDev> &minit) {
     return push_tables(e);
 }
 
+// One coalescence substep of every member: Philox keys, a stable radix sort
+// by (member, key), one thread per pair.
+sdm_status enqueue_coal_substep(sdm_ens *e, const EnsCoalParams &p, int ab, int sub, cudaStream_t st) {
+    const int nm = n_members(e);
+    const int64_t n = e->n_sd;
+    ECK(cudaMemsetAsync(e->live, 0, 4 * (size_t)nm, st), "live counts");
+    if (p.mixed) {
+        uint32_t *k0 = reinterpret_cast<uint32_t *>(e->key[0]), *k1 = reinterpret_cast<uint32_t *>(e->key[1]);
+        k_ens_keys<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, n, sub, k0,
+                                                              e->val[0], e->aux[0], e->acc, e->live);
+        ECK(radix_sort_pairs<uint32_t>(k0, e->val[0], e->aux[0], k1, e->val[1], e->aux[1], n, 4, ab, e->hist,
+                                       e->scan_tmp, st),
+            "sort");
+    } else {
+        k_ens_keys<unsigned long long><<<grid_for(n, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, n, sub,
+                                                                        e->key[0], e->val[0], e->aux[0], e->acc,
+                                                                        e->live);
+        ECK(radix_sort_pairs<unsigned long long>(e->key[0], e->val[0], e->aux[0], e->key[1], e->val[1], e->aux[1], n,
+                                                 8, ab, e->hist, e->scan_tmp, st),
+            "sort");
+    }
+    k_ens_pairs<<<grid_for(n, e->pair_threads), e->pair_threads, 0, st>>>(e->s[e->cur], e->mdev, e->aux[0],
+                                                                           e->val[0], e->acc, e->live, n, p,
+                                                                           e->dstats);
+    return SDM_OK;
+}
+
 sdm_status enqueue_step(sdm_ens *e, const sdm_opts &o) {
     const int nm = n_members(e);
     if (nm == 0) return SDM_OK;
@@ -616,26 +644,8 @@ sdm_status enqueue_step(sdm_ens *e, const sdm_opts &o) {
         EnsCoalParams p{e->eo.dt, o.sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b, o.coal_multi ? 1 : 0};
         const int ab = aux_bytes_for(nm);
         k_ens_ambient<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
-        const int64_t n = e->n_sd;
-        for (int sub = 0; sub < o.sstp_coal; ++sub) {
-            ECK(cudaMemsetAsync(e->live, 0, 4 * (size_t)nm, st), "live counts");
-            if (mixed) {
-                uint32_t *k0 = reinterpret_cast<uint32_t *>(e->key[0]), *k1 = reinterpret_cast<uint32_t *>(e->key[1]);
-                k_ens_keys<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(e->s[e->cur], e->mem[e->cur], e->mdev, n, sub,
-                                                                      k0, e->val[0], e->aux[0], e->acc, e->live);
-                ECK(radix_sort_pairs<uint32_t>(k0, e->val[0], e->aux[0], k1, e->val[1], e->aux[1], n, 4, ab, e->hist,
-                                               e->scan_tmp, st),
-                    "sort");
-            } else {
-                k_ens_keys<unsigned long long><<<grid_for(n, 256), 256, 0, st>>>(
-                    e->s[e->cur], e->mem[e->cur], e->mdev, n, sub, e->key[0], e->val[0], e->aux[0], e->acc, e->live);
-                ECK(radix_sort_pairs<unsigned long long>(e->key[0], e->val[0], e->aux[0], e->key[1], e->val[1],
-                                                         e->aux[1], n, 8, ab, e->hist, e->scan_tmp, st),
-                    "sort");
-            }
-            k_ens_pairs<<<grid_for(n, e->pair_threads), e->pair_threads, 0, st>>>(
-                e->s[e->cur], e->mdev, e->aux[0], e->val[0], e->acc, e->live, n, p, e->dstats);
-        }
+        for (int sub = 0; sub < o.sstp_coal; ++sub)
+            if (sdm_status s = enqueue_coal_substep(e, p, ab, sub, st)) return s;
     }
     k_ens_step_done<<<grid_for(nm, 128), 128, 0, st>>>(e->mdev, nm);
     ECK(cudaGetLastError(), "step");
@@ -721,6 +731,7 @@ sdm_status sdm_ens_create(const sdm_ens_opts *o, void *stream, sdm_ens **out) {
     const int64_t tiles_rs = (e->cap_sd + kRsTileRecords - 1) / kRsTileRecords;
     auto A = [&](void **p, size_t bytes) {
         if (r == cudaSuccess) r = cudaMalloc(p, bytes);
+        if (r == cudaSuccess) e->reserved += bytes;
     };
     for (int b = 0; b < 2; ++b) {
         A((void **)&e->s[b].N, 8 * n);
@@ -760,6 +771,14 @@ sdm_status sdm_ens_create(const sdm_ens_opts *o, void *stream, sdm_ens **out) {
     }
     g_minit[e].clear();
     *out = e;
+    return SDM_OK;
+}
+
+sdm_status sdm_ens_memory(const sdm_ens *e, size_t *device_bytes, int64_t *cap_sd, int32_t *cap_members) {
+    if (!e) return efail(nullptr, SDM_EINVAL, "NULL ensemble");
+    if (device_bytes) *device_bytes = e->reserved;
+    if (cap_sd) *cap_sd = e->cap_sd;
+    if (cap_members) *cap_members = e->cap_members;
     return SDM_OK;
 }
 
@@ -996,7 +1015,8 @@ sdm_status sdm_ens_use_graph(sdm_ens *e, int on) {
     return SDM_OK;
 }
 
-sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *o, int *tile_out, int *threads_out) {
+sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *o, int *tile_out, int *threads_out,
+                            int *pair_threads_out) {
     if (!e || !o) return efail(e, SDM_EINVAL, "NULL argument");
     if (e->in_flight) return efail(e, SDM_ESTATE, "autotune while a step is in flight");
     if (e->dirty_pack) {
@@ -1045,16 +1065,59 @@ sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *o, int *tile_out, int *t
             bth = c[1];
         }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     e->tile = bt;
     e->cond_threads = bth;
     ECK(cudaMemcpyAsync(e->s[e->cur].rw2, e->key[1], 8 * e->n_sd, cudaMemcpyDeviceToDevice, e->stream), "tune");
+    if (sdm_status s = push_tables(e)) return s;
+    // coalescence: the pair kernel's block size over one substep (keys, sort,
+    // pairs), the state kept in the arena's second buffer and put back
+    int bp = e->pair_threads;
+    if (o->coal) {
+        const SdArrays cur = e->s[e->cur], spare = e->s[e->cur ^ 1];
+        const size_t n = (size_t)e->n_sd;
+        auto save = [&](const SdArrays &from, const SdArrays &to) {
+            cudaMemcpyAsync(to.N, from.N, 8 * n, cudaMemcpyDeviceToDevice, e->stream);
+            cudaMemcpyAsync(to.rw2, from.rw2, 8 * n, cudaMemcpyDeviceToDevice, e->stream);
+            cudaMemcpyAsync(to.rd3, from.rd3, 8 * n, cudaMemcpyDeviceToDevice, e->stream);
+            return cudaMemcpyAsync(to.kappa, from.kappa, 8 * n, cudaMemcpyDeviceToDevice, e->stream);
+        };
+        ECK(save(cur, spare), "tune");
+        EnsCoalParams cp{e->eo.dt, o->sstp_coal, e->eo.kernel, mixed ? 1 : 0, e->eo.golovin_b, o->coal_multi ? 1 : 0};
+        const int ab = aux_bytes_for(nm);
+        k_ens_ambient<<<grid_for(nm, 128), 128, 0, e->stream>>>(e->mdev, nm);
+        float bestc = 1e30f;
+        for (int pt : {64, 128, 256, 512}) {
+            e->pair_threads = pt;
+            float tot = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                ECK(save(spare, cur), "tune");
+                cudaEventRecord(a, e->stream);
+                if (sdm_status s = enqueue_coal_substep(e, cp, ab, 0, e->stream)) return s;
+                cudaEventRecord(b, e->stream);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) tot += ms;
+            }
+            if (tot < bestc) {
+                bestc = tot;
+                bp = pt;
+            }
+        }
+        e->pair_threads = bp;
+        ECK(save(spare, cur), "tune");
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     ECK(cudaMemcpyAsync(e->dstats, &saved, sizeof(DevStats), cudaMemcpyHostToDevice, e->stream), "tune");
     ECK(cudaStreamSynchronize(e->stream), "tune");
-    if (sdm_status s = push_tables(e)) return s;
+    if (e->graph) {  // a captured step holds the old launch shapes
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
     if (tile_out) *tile_out = bt;
     if (threads_out) *threads_out = bth;
+    if (pair_threads_out) *pair_threads_out = bp;
     return SDM_OK;
 }
 

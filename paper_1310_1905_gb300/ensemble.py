@@ -11,7 +11,7 @@ from .sdm import (ATTR, INIT, KERNEL, PRECISION, SOLVER, SdmError, load, make_op
 
 SYMBOLS = ["sdm_ens_create", "sdm_ens_destroy", "sdm_ens_last_error", "sdm_ens_add", "sdm_ens_remove",
            "sdm_ens_members", "sdm_ens_step", "sdm_ens_wait", "sdm_ens_moments", "sdm_ens_fields",
-           "sdm_ens_get_attr", "sdm_ens_use_graph", "sdm_ens_autotune", "sdm_ens_stats"]
+           "sdm_ens_get_attr", "sdm_ens_use_graph", "sdm_ens_autotune", "sdm_ens_stats", "sdm_ens_memory"]
 
 
 class sdm_member(C.Structure):
@@ -49,8 +49,9 @@ def _lib():
         L.sdm_ens_fields.argtypes = [e, P(I32), P(D), P(D), I32]
         L.sdm_ens_get_attr.argtypes = [e, I32, C.c_int, V, I64]
         L.sdm_ens_use_graph.argtypes = [e, C.c_int]
-        L.sdm_ens_autotune.argtypes = [e, V, P(C.c_int), P(C.c_int)]
+        L.sdm_ens_autotune.argtypes = [e, V, P(C.c_int), P(C.c_int), P(C.c_int)]
         L.sdm_ens_stats.argtypes = [e, P(sdm_stats)]
+        L.sdm_ens_memory.argtypes = [e, P(C.c_size_t), P(I64), P(I32)]
         for s in SYMBOLS:
             if s != "sdm_ens_last_error":
                 getattr(L, s).restype = C.c_int
@@ -143,15 +144,23 @@ class Ensemble:
         self._check(_lib().sdm_ens_use_graph(self.h, int(on)))
 
     def autotune(self, opts: dict):
+        """Tune and return (condensation tile, its block size, the pair
+        kernel's block size)."""
         o = make_opts(opts)
-        t, th = C.c_int(), C.c_int()
-        self._check(_lib().sdm_ens_autotune(self.h, C.byref(o), C.byref(t), C.byref(th)))
-        return t.value, th.value
+        t, th, pt = C.c_int(), C.c_int(), C.c_int()
+        self._check(_lib().sdm_ens_autotune(self.h, C.byref(o), C.byref(t), C.byref(th), C.byref(pt)))
+        return t.value, th.value, pt.value
 
     def stats(self) -> dict:
         s = sdm_stats()
         self._check(_lib().sdm_ens_stats(self.h, C.byref(s)))
         return s.as_dict()
+
+    def memory(self) -> dict:
+        """Device bytes the arena reserved, and its capacities."""
+        b, n, m = C.c_size_t(), C.c_int64(), C.c_int32()
+        self._check(_lib().sdm_ens_memory(self.h, C.byref(b), C.byref(n), C.byref(m)))
+        return dict(device_bytes=b.value, cap_sd=n.value, cap_members=m.value)
 
     def close(self):
         if self.h:

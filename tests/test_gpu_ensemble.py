@@ -184,8 +184,9 @@ def test_autotune_keeps_state_and_picks_a_launchable_shape(precision):
         e.wait()
     before = [state(tuned, i, m["n_sd"]) for i, m in zip(tid, ms)]
     stats_before = tuned.stats()
-    tile, threads = tuned.autotune(ALL0D)
+    tile, threads, pair_threads = tuned.autotune(ALL0D)
     assert tile in (128, 256, 512, 1024, 2048) and threads in (128, 256, 512)
+    assert pair_threads in (64, 128, 256, 512)
     after = [state(tuned, i, m["n_sd"]) for i, m in zip(tid, ms)]
     for b, a in zip(before, after):
         for k in b:

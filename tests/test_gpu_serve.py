@@ -41,9 +41,15 @@ def test_result_same_alone_and_in_the_mix(precision):
 
 
 def test_admission_by_device_memory_and_latency_report():
+    """The arena is sized by what the ensemble actually reserves
+    (sdm_ens_memory): its reservation fits the budget, and requests wait
+    for room."""
     reqs = requests(16, seed=5, rate=2000.0, steps=(10, 30))
     budget_sd = max(r.member["n_sd"] for r in reqs) * 2
-    srv = Server(mem_budget_bytes=budget_sd * 120, precision="mixed")
+    budget = budget_sd * 130
+    srv = Server(mem_budget_bytes=budget, precision="mixed")
+    assert srv.reserved_bytes <= budget and srv.max_sd >= max(r.member["n_sd"] for r in reqs)
+    assert 100 < srv.bytes_per_sd < 140
     stats = srv.run(reqs)
     assert stats["served"] == 16
     assert srv.peak_resident_sd <= srv.max_sd
