@@ -67,6 +67,7 @@ enum { SDM_INIT_LOGNORMAL = 0, SDM_INIT_EXPONENTIAL = 1 };
 enum { SDM_PRECISION_FP64 = 0, SDM_PRECISION_MIXED = 1 };
 enum { SDM_BACKEND_SERIAL = 0, SDM_BACKEND_OPENMP = 1, SDM_BACKEND_CUDA = 2 };
 enum { SDM_SOLVER_BISECT = 0, SDM_SOLVER_FAST = 1 };
+enum { SDM_COND_AUTO = 0, SDM_COND_FUSED = 1, SDM_COND_STAGED = 2 };
 
 /* Options fixed for the life of a simulation (opts_init_t, Sec. 5.2.1).
  * nx, ny, nz: cells per dimension, 0 = dimension absent (all 0: parcel/box,
@@ -92,7 +93,23 @@ enum { SDM_SOLVER_BISECT = 0, SDM_SOLVER_FAST = 1 };
  *   FP64 throughout; SDM_SOLVER_FAST (the default in the bindings) takes the
  *   same bracket, the same midpoints and the same sign decisions, decided in
  *   FP32 where an error bound proves the sign, then finishes with a
- *   bracketed FP64 Newton/secant iteration to the same sign change. */
+ *   bracketed FP64 Newton/secant iteration to the same sign change.
+ * cond_layout: how the fast FP64 condensation runs on the GPU, with the same
+ *   result per super-droplet: SDM_COND_FUSED, one kernel per step carrying
+ *   every solve; SDM_COND_STAGED, per substep a chain of small kernels (FP32
+ *   starts, rounds of FP64 evaluations over compacted lists, the cell
+ *   sums); SDM_COND_AUTO (0) picks by domain size.  Other solvers and the
+ *   mixed mode always run fused.
+ * sd_reserve: extra super-droplet slots (N = 0) beyond the initial ones,
+ *   kept free for arrivals from the neighbouring slabs of an x_open context
+ *   (sdm_import): their ids carry the top bit (2^31), which marks a slot
+ *   recycling leaves alone.  0 by default.
+ * x_open: 0 (default): periodic in x.  1: the context is one slab of a
+ *   domain decomposed in x (the paper has no counterpart; in its calling
+ *   sequence, Sec. 5.2, decomposition is the solver's): super-droplets advected past x = 0 or
+ *   x = nx dx keep their position, outside [0, nx dx), until
+ *   sdm_export_leavers takes them out, and the Courant numbers of the two
+ *   boundary edges divide by the rho_d of their one adjacent cell. */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz, dt;
@@ -108,6 +125,9 @@ typedef struct {
     int precision;
     int backend;
     int cond_solver;
+    int x_open;
+    int cond_layout;
+    int64_t sd_reserve;
 } sdm_opts_init;
 
 /* Per-step options (opts_t, Sec. 5.2.1; defaults 1,1,1,1, 44, 10, 10, 0, 0):
@@ -320,6 +340,58 @@ sdm_status sdm_get_fields(sdm_ctx *ctx, double *th, double *rv);
 sdm_status sdm_get_step(const sdm_ctx *ctx, uint64_t *step);
 sdm_status sdm_set_step(sdm_ctx *ctx, uint64_t step);
 
+/* ---- decomposed domains: the exchange of super-droplets between slabs ----
+ * The paper's library holds one domain and leaves decomposition to the
+ * solver that calls it (Sec. 5.2, example calling sequence); these calls are
+ * the device side of the exchange a
+ * sharded driver needs (the paper has no counterpart).  With x_open set, a
+ * timestep is: sdm_step_sync; sdm_step_transport (recycling, advection,
+ * sedimentation); sdm_export_leavers, the exchange with the neighbouring
+ * slabs (decomp.exchange in the Python package), sdm_import; then
+ * sdm_step_coalesce (regrouping and coalescence) and sdm_wait.  Without
+ * exports or imports sdm_step_transport + sdm_step_coalesce give the
+ * results of sdm_step_async bit for bit. */
+
+/* A block of super-droplets in flight between contexts: n entries per array.
+ * y or z may be NULL when the context lacks that dimension.  on_device: 1 =
+ * device memory of the context's GPU, 0 = host memory. */
+typedef struct {
+    uint64_t *N;
+    uint32_t *uid;
+    double *rw2, *rd3, *kappa, *x, *y, *z;
+    int on_device;
+} sdm_sd_block;
+
+/* The first half of sdm_step_async: recycling of zero multiplicities,
+ * advection and sedimentation with exits (Sec. 5.1.2, 5.1.4, 5.1.5),
+ * enqueued on the context's stream.  SDM_ESTATE while an sdm_step_async or
+ * sdm_step_coalesce is in flight or a transport is pending. */
+sdm_status sdm_step_transport(sdm_ctx *ctx, const sdm_opts *opts);
+
+/* The second half: regrouping by cell (from the positions, if super-droplets
+ * were exported or imported in between) and sstp_coal coalescence substeps
+ * (opts->coal), then the step counter advances; complete with sdm_wait.
+ * SDM_ESTATE without a pending sdm_step_transport. */
+sdm_status sdm_step_coalesce(sdm_ctx *ctx, const sdm_opts *opts);
+
+/* Take out every super-droplet with N > 0 and x outside [0, nx dx) (only
+ * an x_open context has such): their attributes go to dst, in storage
+ * order, and their slots are left with N = 0 for sdm_import to fill; the
+ * emptied slot's id gets the top bit (2^31), the mark of a slot
+ * that recycling leaves to arrivals (the leaver keeps its id, which must
+ * stay unique among live super-droplets).  cap: the block's room; *n_out:
+ * how many were taken.  Completes
+ * before returning.  SDM_ENOMEM (nothing taken, *n_out the number waiting)
+ * if cap is too small, SDM_EINVAL if the context is not x_open. */
+sdm_status sdm_export_leavers(sdm_ctx *ctx, sdm_sd_block dst, int64_t cap, int64_t *n_out);
+
+/* Put n super-droplets (attributes as sdm_export_leavers writes them, x
+ * already in this context's coordinates, [0, nx dx); ids below 2^31) into
+ * slots with N = 0, the k-th into the k-th such slot in storage order.  Completes before
+ * returning.  SDM_ENOMEM (nothing written) if fewer than n slots are free,
+ * SDM_EINVAL for a position outside the domain. */
+sdm_status sdm_import(sdm_ctx *ctx, sdm_sd_block src, int64_t n);
+
 /* ---- regrouping of caller-held particles -------------------------------- */
 
 /* Counting sort of particles by grid cell, the regrouping that the cell-wise
@@ -421,6 +493,12 @@ typedef struct {
 
 sdm_status sdm_ens_create(const sdm_ens_opts *opts, void *stream, sdm_ens **out);
 sdm_status sdm_ens_destroy(sdm_ens *e);
+/* The device memory the ensemble's arena reserved at creation (held until
+ * sdm_ens_destroy), its capacity in super-droplets and in members: what a
+ * server admits requests against.  A repacking after removals also takes,
+ * for its duration, a few bytes per member more.  The paper has no
+ * counterpart (serving). */
+sdm_status sdm_ens_memory(const sdm_ens *e, size_t *device_bytes, int64_t *cap_sd, int32_t *cap_members);
 const char *sdm_ens_last_error(const sdm_ens *e);
 
 /* Admit a member (initialised on the device, Sec. 5.1.6); *id receives its
@@ -462,9 +540,14 @@ sdm_status sdm_ens_get_attr(sdm_ens *e, int32_t id, int attr, void *dst, int64_t
  * change. */
 sdm_status sdm_ens_use_graph(sdm_ens *e, int on);
 
-/* Choose the condensation tile size and block shape by timing candidate
- * shapes on the resident members (their state is restored afterwards). */
-sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *opts, int *tile_out, int *threads_out);
+/* Choose the launch shapes by timing candidates on the resident members
+ * (their state and counters are restored afterwards): the condensation tile
+ * size and block size (one substep's solves), then, if opts->coal, the
+ * block size of the coalescence pair kernel (one substep's keys, sort and
+ * pairs).  A captured step graph is dropped and re-captured at the next
+ * step.  Outputs may be NULL.  The paper has no counterpart (batching). */
+sdm_status sdm_ens_autotune(sdm_ens *e, const sdm_opts *opts, int *tile_out, int *threads_out,
+                            int *pair_threads_out);
 
 /* Counters accumulated over all members since creation. */
 sdm_status sdm_ens_stats(sdm_ens *e, sdm_stats *out);

@@ -1064,6 +1064,217 @@ static void launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) 
     else launch_condense_lpc<32, MODE>(c, o, B);
 }
 
+// ---------------------------------------------------------------------------
+// Staged condensation (FP64, fast solver), for domains of many cells: each
+// substep is a chain of small kernels instead of one kernel that carries a
+// super-droplet's whole solve.  (1) the cells' ambient state; (2) every
+// super-droplet's FP32 start (fs_start), its solve state written to a record;
+// (3) rounds of FP64 growth evaluations over compacted lists of the records
+// that still need one, each round one evaluation per record (so the lanes of
+// a warp do the same work), finished solves writing their r_w^2; (4) per
+// cell, the sum of eq. rhov_update and the update of r_v and theta.  The
+// solve's steps are those of solve_rw2_fast, in the same order on the same
+// values, so each super-droplet's result is the same bit for bit; the cell
+// sums add the same terms in another order.  The solve state travels
+// through HBM between the kernels, which the FP64-bound fused kernel leaves
+// idle.
+enum { kTaskNone = 0, kTaskG0Euler = 1, kTaskG0Tiny = 2, kTaskG0Exact = 3, kTaskPolish = 4 };
+
+struct StagedRec {
+    FastSolve S;
+    uint32_t sd;
+    int task;
+};
+
+struct StagedCell {
+    Thermo t;
+    ThermoF tf;
+};
+
+constexpr int kStagedRounds = 15;  // a fast solve takes at most 14 FP64 growth evaluations
+constexpr int64_t kStagedMinSd = int64_t(1) << 62;  // the automatic choice: set from measurement
+
+__global__ void k_cs_cells(const double *th, const double *rv, const double *rhod, int n_cells, double RH_max,
+                           StagedCell *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    const Thermo t = thermo_cond(th[c], rv[c], rhod[c], RH_max, rhod_factor(rhod[c]));
+    out[c].t = t;
+    out[c].tf = to_float(t);
+}
+
+// one warp per cell: every super-droplet's FP32 start; the record at its
+// storage index (round 0 takes every index)
+__global__ void k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells, double dtp,
+                           int physics, StagedRec *rec, double *x1, unsigned *count0, unsigned n_sd) {
+    const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c64 == 0 && threadIdx.x == 0) *count0 = n_sd;  // round 0 takes every record
+    if (c64 >= n_cells) return;
+    const int c = (int)c64, lane = threadIdx.x & 31;
+    const ThermoF &tf = cells[c].tf;
+    for (uint32_t i = offset[c] + lane; i < offset[c + 1]; i += 32) {
+        StagedRec &r = rec[i];
+        r.sd = i;
+        const double x0 = s.rw2[i];
+        if (s.N[i] == 0) {
+            r.task = kTaskNone;
+            x1[i] = x0;
+            continue;
+        }
+        FastSolve S;
+        S.x0 = x0;
+        S.rd3 = s.rd3[i];
+        S.kappa = s.kappa[i];
+        const int st = fs_start(S, tf, dtp, physics);
+        r.task = st == kStartPolish  ? kTaskPolish
+                 : st == kStartExact ? kTaskG0Exact
+                 : st == kStartEuler ? kTaskG0Euler
+                                     : kTaskG0Tiny;
+        r.S = S;
+    }
+}
+
+// one FP64 growth evaluation per record; the records that need another go
+// to the next list (one atomic per block), the finished write r_w^2
+__global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, StagedRec *out,
+                                                 unsigned *n_out, const uint32_t *cell_of_sd, const StagedCell *cells,
+                                                 double dtp, int physics, double *x1, DevStats *st) {
+    __shared__ unsigned s_warp[8], s_base;
+    const unsigned n = *n_in;
+    SolveCounters cnt{0, 0, 0};
+    bool bad = false;
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const unsigned t = base + threadIdx.x;
+        bool keep = false;
+        StagedRec r;
+        if (t < n) {
+            r = in[t];
+            if (r.task != kTaskNone) {
+                const StagedCell &cl = cells[cell_of_sd[r.sd]];
+                FastSolve &S = r.S;
+                const bool g0 = r.task != kTaskPolish;
+                cnt.evals++;
+                double mag;
+                const double v = growth_eval(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag);
+                bool done;
+                if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
+                    if (r.task == kTaskG0Euler) cnt.euler++;
+                    S.x1 = fs_euler(S, v, dtp);
+                    done = true;
+                } else if (r.task == kTaskG0Exact) {
+                    done = fs_after_g0(S, v, cl.t, cl.tf, dtp, physics, cnt);
+                } else {
+                    done = fs_after_polish(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
+                }
+                if (done) {
+                    x1[r.sd] = S.x1;
+                    bad |= !isfinite(S.x1);
+                } else {
+                    r.task = kTaskPolish;
+                    keep = true;
+                }
+            }
+        }
+        // block-wide compaction of the records that continue
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) s_warp[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                const unsigned v = s_warp[q];
+                s_warp[q] = tot;
+                tot += v;
+            }
+            s_base = tot ? atomicAdd(n_out, tot) : 0u;
+        }
+        __syncthreads();
+        if (keep) out[s_base + s_warp[w] + __popc(m & ((1u << lane) - 1u))] = r;
+        __syncthreads();
+    }
+    const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
+    const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
+    const unsigned anybad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (ne) atomicAdd(&st->n_euler, (unsigned long long)ne);
+        if (nf) atomicAdd(&st->n_fallback, (unsigned long long)nf);
+        if (anybad) atomicOr(&st->flags, kFlagNumeric);
+    }
+}
+
+// one warp per cell: eq. rhov_update with the new radii, in a fixed order
+__global__ void k_cs_update(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells,
+                            const double *x1, double *th, double *rv, const double *rhod, double dV, DevStats *st) {
+    const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c64 >= n_cells) return;
+    const int c = (int)c64, lane = threadIdx.x & 31;
+    double sum = 0.0;
+    for (uint32_t i = offset[c] + lane; i < offset[c + 1]; i += 32) {
+        const unsigned long long N = s.N[i];
+        const double x0 = s.rw2[i], xn = x1[i];
+        if (N != 0) sum += (double)N * (xn * sqrt(xn) - x0 * sqrt(x0));
+        s.rw2[i] = xn;
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) {
+        const Thermo &t = cells[c].t;
+        const double drv = -4.0 * phys::pi * phys::rho_w / (3.0 * dV * rhod[c]) * sum;
+        const double rvn = t.rv + drv, thn = t.th + drv * t.dth_drv;
+        rv[c] = rvn;
+        th[c] = thn;
+        if (!isfinite(rvn) || !isfinite(thn)) atomicOr(&st->flags, kFlagNumeric);
+    }
+}
+
+__global__ void k_cs_cellmap(const uint32_t *offset, int n_cells, uint32_t *cell_of_sd) {
+    const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c64 >= n_cells) return;
+    const int c = (int)c64;
+    for (uint32_t i = offset[c] + (threadIdx.x & 31); i < offset[c + 1]; i += 32) cell_of_sd[i] = (uint32_t)c;
+}
+
+static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
+    const int64_t n = c->n_sd;
+    const int nc = c->grid.n_cells;
+    cudaError_t e = cudaSuccess;
+    if (!c->cs_rec[0]) {
+        e = cudaMalloc(&c->cs_rec[0], sizeof(StagedRec) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_rec[1], sizeof(StagedRec) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cell, sizeof(StagedCell) * (size_t)nc + 4 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_x1, 8 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedRounds + 2));
+        if (e != cudaSuccess) return e;
+    }
+    StagedRec *rec[2] = {(StagedRec *)c->cs_rec[0], (StagedRec *)c->cs_rec[1]};
+    StagedCell *cells = (StagedCell *)c->cs_cell;
+    uint32_t *cell_of_sd = (uint32_t *)(cells + nc);
+    const double dtp = c->grid.dt / o.sstp_cond;
+    const int64_t warps_threads = (int64_t)nc * 32;
+    const int B = 128;
+    k_cs_cellmap<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->offset, nc, cell_of_sd);
+    int dev = 0, n_sm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int eval_blocks = n_sm * 8;
+    for (int sub = 0; sub < o.sstp_cond; ++sub) {
+        k_cs_cells<<<grid_for(nc, 128), 128, 0, c->stream>>>(c->th, c->rv, c->rhod, nc, o.RH_max, cells);
+        // round 0 takes every record (count n); each round's survivors feed the next
+        e = cudaMemsetAsync(c->cs_cnt, 0, 4 * (kStagedRounds + 2), c->stream);
+        if (e != cudaSuccess) return e;
+        k_cs_start<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, dtp,
+                                                                   c->oi.physics, rec[0], c->cs_x1, c->cs_cnt,
+                                                                   (unsigned)n);
+        for (int r = 0; r < kStagedRounds; ++r)
+            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], c->cs_cnt + r, rec[(r + 1) & 1],
+                                                          c->cs_cnt + r + 1, cell_of_sd, cells, dtp, c->oi.physics,
+                                                          c->cs_x1, c->dstats);
+        k_cs_update<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, c->cs_x1,
+                                                                    c->th, c->rv, c->rhod, c->grid.dV, c->dstats);
+    }
+    return cudaGetLastError();
+}
+
 // Lanes per cell: 4, 8 or 32 (about eight super-droplets per lane), raised
 // while the launch has fewer than ~54 warps per SM (152 SMs), since one
 // lane's solves run in sequence and the FP64 pipe needs several warps per
@@ -1071,6 +1282,12 @@ static void launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) 
 // fine-grained.
 cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
     const int64_t per_cell = (int64_t)c->G * c->oi.sd_conc, n_cells = c->grid.n_cells;
+    // the staged chain for the fast FP64 solve where chosen (cond_layout), or
+    // by default where the domain holds at least 2^22 super-droplets
+    const bool fast64 = c->oi.precision != SDM_PRECISION_MIXED && c->oi.cond_solver != SDM_SOLVER_BISECT;
+    const bool staged = c->oi.cond_layout == SDM_COND_STAGED ||
+                        (c->oi.cond_layout == SDM_COND_AUTO && c->n_sd >= kStagedMinSd);
+    if (fast64 && staged) return launch_condense_staged(c, o);
     int lpc = per_cell <= 32 ? 4 : (per_cell <= 64 ? 8 : 32);
     while (lpc < 32 && n_cells * lpc < (int64_t)32 * 8192) lpc = lpc == 4 ? 8 : 32;
     const int B = n_cells * lpc < (int64_t)32 * 32768 ? 32 : 128;

@@ -94,6 +94,22 @@ __global__ void k_init_offsets(uint32_t *offset, int n_cells, uint32_t per_cell)
     if (c <= n_cells) offset[c] = (uint32_t)c * per_cell;
 }
 
+// the reserved slots (sdm_opts_init::sd_reserve) after the initial ones:
+// N = 0, no water, at the domain's origin, ids after the initial ones with
+// the mark of a slot kept for arrivals
+__global__ void k_init_reserve(SdArrays s, int64_t first, int64_t n, Grid g) {
+    const int64_t q = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    s.N[q] = 0;
+    s.rw2[q] = 0.0;
+    s.rd3[q] = 0.0;
+    s.kappa[q] = 0.0;
+    if (g.nx > 0) s.x[q] = 0.0;
+    if (g.ny > 0) s.y[q] = 0.0;
+    if (g.nz > 0) s.z[q] = 0.0;
+    s.uid[q] = (uint32_t)q | kUidVacant;
+}
+
 cudaError_t launch_init(sdm_ctx *c) {
     InitParams p{};
     p.g = c->grid;
@@ -116,8 +132,10 @@ cudaError_t launch_init(sdm_ctx *c) {
         p.lmax[g] = c->lnr_max.empty() ? 0.0 : c->lnr_max[g];
     }
     const int B = 256;
-    k_init<<<grid_for(c->n_sd, B), B, 0, c->stream>>>(c->buf[c->cur], c->n_sd, p, c->th, c->rv,
-                                                       c->rhod);
+    const int64_t n_init = c->n_sd - c->oi.sd_reserve;
+    k_init<<<grid_for(n_init, B), B, 0, c->stream>>>(c->buf[c->cur], n_init, p, c->th, c->rv, c->rhod);
+    if (c->oi.sd_reserve > 0)
+        k_init_reserve<<<grid_for(c->oi.sd_reserve, B), B, 0, c->stream>>>(c->buf[c->cur], n_init, c->n_sd, c->grid);
     k_init_offsets<<<grid_for(c->grid.n_cells + 1, B), B, 0, c->stream>>>(
         c->offset, c->grid.n_cells, (uint32_t)(c->G * c->oi.sd_conc));
     return cudaGetLastError();

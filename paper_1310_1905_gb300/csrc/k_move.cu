@@ -34,10 +34,12 @@ __device__ __forceinline__ int cell_of(const Grid &g, double x, double y, double
 }
 
 // Courant number on an edge: rho_d C divided by the mean rho_d of the two
-// cells sharing the edge (the adjacent cell on a closed boundary)
+// cells sharing the edge (the adjacent cell on a closed boundary, and on the
+// x boundaries of a slab)
 __device__ __forceinline__ double courant_x(const Grid &g, const double *rhod, const double *C,
                                             int ie, int j, int k) {
-    const int il = (ie - 1 + g.nx) % g.nx, ir = ie % g.nx;
+    const int il = g.x_open ? (ie > 0 ? ie - 1 : 0) : (ie - 1 + g.nx) % g.nx;
+    const int ir = g.x_open ? (ie < g.nx ? ie : g.nx - 1) : ie % g.nx;
     const double re = 0.5 * (rhod[((int64_t)il * g.NY + j) * g.NZ + k] +
                              rhod[((int64_t)ir * g.NY + j) * g.NZ + k]);
     return C[((int64_t)ie * g.NY + j) * g.NZ + k] / re;
@@ -133,10 +135,11 @@ __global__ void k_move(SdArrays s, int64_t n, MoveParams p, const double *rhod, 
             vt = p.mixed ? (double)vterm_f((float)s.rw2[q], (float)amb[2 * c], (float)amb[2 * c + 1])
                          : vterm(s.rw2[q], amb[2 * c], amb[2 * c + 1]);
         if (p.adve) {
-            if (g.nx > 0 && p.Cx)
-                x = wrap(advect_1d(x, g.dx, i, p.Cx[((int64_t)i * g.NY + j) * g.NZ + k],
-                                   p.Cx[((int64_t)(i + 1) * g.NY + j) * g.NZ + k]),
-                         g.nx * g.dx);
+            if (g.nx > 0 && p.Cx) {
+                x = advect_1d(x, g.dx, i, p.Cx[((int64_t)i * g.NY + j) * g.NZ + k],
+                              p.Cx[((int64_t)(i + 1) * g.NY + j) * g.NZ + k]);
+                if (!g.x_open) x = wrap(x, g.nx * g.dx);  // a slab keeps its leavers outside for the export
+            }
             if (g.ny > 0 && p.Cy)
                 y = wrap(advect_1d(y, g.dy, j, p.Cy[((int64_t)i * (g.NY + 1) + j) * g.NZ + k],
                                    p.Cy[((int64_t)i * (g.NY + 1) + j + 1) * g.NZ + k]),

@@ -21,7 +21,7 @@ __global__ void k_rc_compact(SdArrays s, int64_t n, SortRec *zrec, DevStats *st)
     bool donor = false;
     if (i < n) {
         const unsigned long long N = s.N[i];
-        if (N == 0) {
+        if (N == 0 && !(s.uid[i] & kUidVacant)) {  // a slot kept for arrivals is no zero to fill
             const unsigned q = atomicAdd(&st->n_rc_zero, 1u);
             zrec[q] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
         }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_rc_small(SdArrays s, int n, DevStats *
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long N = s.N[i];
-        if (N == 0) {
+        if (N == 0 && !(s.uid[i] & kUidVacant)) {
             r[atomicAdd(&s_m, 1u)] = SortRec{(unsigned long long)s.uid[i], 0u, (uint32_t)i};
             atomicAdd(&s_nz, 1u);
         } else if (N >= 2) {

@@ -216,6 +216,9 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->slot);
     cudaFree(c->perm);
     cudaFree(c->count);
+    cudaFree(c->xch_flag);
+    cudaFree(c->xch_off);
+    cudaFree(c->xch_tmp);
     cudaFree(c->offset);
     cudaFree(c->bigcells);
     cudaFree(c->th);
@@ -225,6 +228,11 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->outbuf);
     cudaFree(c->spec_buf);
     cudaFree(c->spec_edges);
+    cudaFree(c->cs_rec[0]);
+    cudaFree(c->cs_rec[1]);
+    cudaFree(c->cs_cell);
+    cudaFree(c->cs_x1);
+    cudaFree(c->cs_cnt);
     cudaFree(c->cond_order);
     cudaFree(c->cond_cost);
     cudaFree(c->euler_tmp);
@@ -352,6 +360,8 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
         return fail(nullptr, SDM_EINVAL, "unknown precision mode");
     if (oi->cond_solver != SDM_SOLVER_BISECT && oi->cond_solver != SDM_SOLVER_FAST)
         return fail(nullptr, SDM_EINVAL, "unknown condensation solver");
+    if (oi->cond_layout < SDM_COND_AUTO || oi->cond_layout > SDM_COND_STAGED)
+        return fail(nullptr, SDM_EINVAL, "unknown condensation layout");
     if (oi->init_dist == SDM_INIT_LOGNORMAL) {
         if (oi->n_modes < 1 || oi->n_modes > kMaxModes || !oi->modes)
             return fail(nullptr, SDM_EINVAL, "lognormal initialisation needs 1..8 modes");
@@ -390,6 +400,7 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
     g.dz = oi->dz;
     g.dt = oi->dt;
     g.dV = oi->dx * oi->dy * oi->dz;
+    g.x_open = oi->x_open && oi->nx > 0 ? 1 : 0;
     const int64_t ncell = (int64_t)g.NX * g.NY * g.NZ;
     if (ncell > (1LL << 30)) {
         free_ctx(c);
@@ -416,7 +427,11 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
         c->gkappa.push_back(0.0);
     }
     c->G = (int)c->gkappa.size();
-    c->n_sd = ncell * c->G * oi->sd_conc;
+    if (oi->sd_reserve < 0) {
+        free_ctx(c);
+        return fail(nullptr, SDM_EINVAL, "sd_reserve must be >= 0");
+    }
+    c->n_sd = ncell * c->G * oi->sd_conc + oi->sd_reserve;
     if (c->n_sd >= (1LL << 32) - 1) {
         free_ctx(c);
         return fail(nullptr, SDM_EINVAL, "more than 2^32 - 2 super-droplets");
@@ -496,6 +511,8 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
     if (st == SDM_OK) {
         e = launch_init(c);
         if (e == cudaSuccess) e = launch_ambient(c);
+        // the reserved slots sit apart from the per-cell ranges: regroup first
+        c->layout_dirty = c->oi.sd_reserve > 0;
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             st = SDM_ECUDA;
@@ -625,10 +642,12 @@ sdm_status sdm_step_sync(sdm_ctx *c, const sdm_opts *o, sdm_arr th, sdm_arr rv, 
     return SDM_OK;
 }
 
-sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
-    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
-    if (sdm_status s = check_opts(c, o)) return s;
-    if (c->async_in_flight) return fail(c, SDM_ESTATE, "step_async called twice without sdm_wait");
+}  // extern "C"
+
+namespace {
+
+// The first half of a step_async: recycling, advection, sedimentation.
+sdm_status enqueue_transport(sdm_ctx *c, const sdm_opts *o) {
     if (c->layout_dirty)
         if (sdm_status s = regroup(c)) return s;
     if (c->known_zeros > 0 && recycle_small(c)) {  // one block, no count through the host
@@ -651,6 +670,19 @@ sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
         CK(launch_move(c, *o), "move");
         c->tacc.launches += 2 + (o->adve && (c->rhoC[0] || c->rhoC[1] || c->rhoC[2]) ? 1 : 0);  // + k_courant
     }
+    return SDM_OK;
+}
+
+// The second half: regrouping and coalescence.  After an export or import
+// the cells and counting-sort slots are taken afresh from the positions.
+sdm_status enqueue_coalesce(sdm_ctx *c, const sdm_opts *o) {
+    if (c->layout_dirty) {
+        Phase ph(c, PH_MOVE);
+        const sdm_opts still{0, 0, 0, 0, 44.0, 1, 1};
+        CK(launch_move(c, still), "cells");
+        c->tacc.launches += 1;
+        c->layout_dirty = false;
+    }
     {
         Phase ph(c, PH_SORT);
         CK(launch_regroup(c), "scan");
@@ -666,6 +698,140 @@ sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
     c->step++;
     CK(cudaEventRecord(c->done_event, c->stream), "event");
     c->async_in_flight = true;
+    return SDM_OK;
+}
+
+// a block of n super-droplets in device memory: dst itself, or a staging
+// copy of a host block (alloc, and fill from the host when upload)
+struct DevBlock {
+    sdm_sd_block b{};
+    void *mem = nullptr;
+    ~DevBlock() { cudaFree(mem); }
+};
+
+cudaError_t device_block(sdm_ctx *c, const sdm_sd_block &host, int64_t n, bool upload, DevBlock &out) {
+    if (host.on_device) {
+        out.b = host;
+        return cudaSuccess;
+    }
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    cudaError_t e = cudaMalloc(&out.mem, m * (8 + 4 + 6 * 8));
+    if (e != cudaSuccess) return e;
+    char *p = (char *)out.mem;
+    out.b.N = (uint64_t *)p;
+    p += 8 * m;
+    double *d = (double *)p;
+    out.b.rw2 = d;
+    out.b.rd3 = d + m;
+    out.b.kappa = d + 2 * m;
+    out.b.x = d + 3 * m;
+    out.b.y = d + 4 * m;
+    out.b.z = d + 5 * m;
+    out.b.uid = (uint32_t *)(d + 6 * m);
+    out.b.on_device = 1;
+    if (upload && n > 0) {
+        const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(out.b.N, host.N, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.b.uid, host.uid, 4 * n, h2d, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.b.rw2, host.rw2, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.b.rd3, host.rd3, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.b.kappa, host.kappa, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.b.x, host.x, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess && c->grid.ny > 0) e = cudaMemcpyAsync(out.b.y, host.y, 8 * n, h2d, c->stream);
+        if (e == cudaSuccess && c->grid.nz > 0) e = cudaMemcpyAsync(out.b.z, host.z, 8 * n, h2d, c->stream);
+    }
+    return e;
+}
+
+bool block_complete(const sdm_ctx *c, const sdm_sd_block &b) {
+    return b.N && b.uid && b.rw2 && b.rd3 && b.kappa && b.x && (c->grid.ny == 0 || b.y) && (c->grid.nz == 0 || b.z);
+}
+
+}  // namespace
+
+extern "C" {
+
+sdm_status sdm_step_async(sdm_ctx *c, const sdm_opts *o) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (sdm_status s = check_opts(c, o)) return s;
+    if (c->async_in_flight) return fail(c, SDM_ESTATE, "step_async called twice without sdm_wait");
+    if (c->transported) return fail(c, SDM_ESTATE, "step_async with a transport pending (sdm_step_coalesce)");
+    if (sdm_status s = enqueue_transport(c, o)) return s;
+    return enqueue_coalesce(c, o);
+}
+
+sdm_status sdm_step_transport(sdm_ctx *c, const sdm_opts *o) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (sdm_status s = check_opts(c, o)) return s;
+    if (c->async_in_flight) return fail(c, SDM_ESTATE, "step_transport before sdm_wait of the previous step");
+    if (c->transported) return fail(c, SDM_ESTATE, "step_transport twice without sdm_step_coalesce");
+    if (sdm_status s = enqueue_transport(c, o)) return s;
+    c->transported = true;
+    return SDM_OK;
+}
+
+sdm_status sdm_step_coalesce(sdm_ctx *c, const sdm_opts *o) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (sdm_status s = check_opts(c, o)) return s;
+    if (!c->transported) return fail(c, SDM_ESTATE, "step_coalesce without sdm_step_transport");
+    c->transported = false;
+    return enqueue_coalesce(c, o);
+}
+
+sdm_status sdm_export_leavers(sdm_ctx *c, sdm_sd_block dst, int64_t cap, int64_t *n_out) {
+    if (!c || !n_out) return fail(c, SDM_EINVAL, "NULL argument");
+    *n_out = 0;
+    if (!c->grid.x_open) return fail(c, SDM_EINVAL, "export_leavers needs an x_open context");
+    if (c->async_in_flight) return fail(c, SDM_ESTATE, "export while a step is in flight");
+    if (c->layout_dirty && !c->transported)
+        if (sdm_status s = regroup(c)) return s;
+    uint32_t cnt = 0;
+    CK(launch_exchange_count(c, 1, &cnt), "leavers");
+    *n_out = cnt;
+    if ((int64_t)cnt > cap) return fail(c, SDM_ENOMEM, "the block holds fewer super-droplets than leave");
+    if (cnt == 0) return SDM_OK;
+    if (!block_complete(c, dst)) return fail(c, SDM_EINVAL, "a block array is NULL");
+    DevBlock db;
+    CK(device_block(c, dst, cnt, false, db), "export staging");
+    CK(launch_export(c, db.b), "export");
+    if (!dst.on_device) {
+        const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(dst.N, db.b.N, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        CK(cudaMemcpyAsync(dst.uid, db.b.uid, 4 * (size_t)cnt, d2h, c->stream), "export copy");
+        CK(cudaMemcpyAsync(dst.rw2, db.b.rw2, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        CK(cudaMemcpyAsync(dst.rd3, db.b.rd3, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        CK(cudaMemcpyAsync(dst.kappa, db.b.kappa, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        CK(cudaMemcpyAsync(dst.x, db.b.x, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        if (c->grid.ny > 0) CK(cudaMemcpyAsync(dst.y, db.b.y, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+        if (c->grid.nz > 0) CK(cudaMemcpyAsync(dst.z, db.b.z, 8 * (size_t)cnt, d2h, c->stream), "export copy");
+    }
+    CK(cudaStreamSynchronize(c->stream), "export");
+    c->known_zeros += cnt;
+    c->layout_dirty = true;
+    return SDM_OK;
+}
+
+sdm_status sdm_import(sdm_ctx *c, sdm_sd_block src, int64_t n) {
+    if (!c) return fail(nullptr, SDM_EINVAL, "NULL context");
+    if (n < 0) return fail(c, SDM_EINVAL, "n must be >= 0");
+    if (c->async_in_flight) return fail(c, SDM_ESTATE, "import while a step is in flight");
+    if (n == 0) return SDM_OK;
+    if (!block_complete(c, src)) return fail(c, SDM_EINVAL, "a block array is NULL");
+    if (c->layout_dirty && !c->transported)
+        if (sdm_status s = regroup(c)) return s;
+    DevBlock db;
+    CK(device_block(c, src, n, true, db), "import staging");
+    unsigned bad = 0;
+    CK(launch_block_check(c, db.b, n, &bad), "import check");
+    if (bad)
+        return fail(c, SDM_EINVAL, "an arriving super-droplet has N = 0, an id >= 2^31 or a position outside the domain");
+    uint32_t free_slots = 0;
+    CK(launch_exchange_count(c, 0, &free_slots), "free slots");
+    if ((int64_t)free_slots < n) return fail(c, SDM_ENOMEM, "fewer free slots (N = 0) than arrivals");
+    CK(launch_import(c, db.b, n), "import");
+    CK(cudaStreamSynchronize(c->stream), "import");
+    c->known_zeros = free_slots - (uint64_t)n;
+    c->layout_dirty = true;
     return SDM_OK;
 }
 

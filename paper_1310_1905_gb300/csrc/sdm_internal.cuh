@@ -283,6 +283,11 @@ struct DevStats {
     unsigned long long n_coal_substeps;  // cell-substeps of coalescence taken
 };
 enum : unsigned { kFlagNumeric = 1u, kFlagBigCell = 2u };
+// The top bit of an id marks a free slot kept for arrivals from other slabs
+// (sdm_export_leavers leaves it on the slot it empties; sd_reserve slots
+// start with it): recycling leaves such slots alone, sdm_import overwrites
+// the id.  Live super-droplets' ids stay below 2^31.
+constexpr uint32_t kUidVacant = 0x80000000u;
 
 struct Grid {
     int nx, ny, nz;     // 0 = absent
@@ -290,6 +295,7 @@ struct Grid {
     double dx, dy, dz;  // cell sizes
     double dt, dV;
     int n_cells;
+    int x_open;         // 1: a slab of a domain decomposed in x (no periodic wrap in x)
 };
 
 struct SdArrays {  // one buffer of the structure-of-arrays state
@@ -334,10 +340,16 @@ struct sdm_ctx {
 
     bool async_in_flight = false;
     bool layout_dirty = false;
+    bool transported = false;   // sdm_step_transport done, sdm_step_coalesce pending
+    uint32_t *xch_flag = nullptr, *xch_off = nullptr, *xch_tmp = nullptr;  // exchange scratch (n_sd + 1)
     bool rng_set = false;
     int diag_wet = 1;
     double diag_rmin = 0.0, diag_rmax = 0.0;
     double *spec_buf = nullptr, *spec_edges = nullptr;  // binned spectrum: n_bins x n_cells, n_bins + 1
+    void *cs_rec[2] = {nullptr, nullptr};               // staged condensation: solve records, ping-pong
+    void *cs_cell = nullptr;                            // and the per-cell ambient state
+    double *cs_x1 = nullptr;                            // and each super-droplet's new r_w^2
+    unsigned *cs_cnt = nullptr;                         // and the round counts
     uint32_t *cond_order = nullptr;                     // condensation: warps longest-first
     float *cond_cost = nullptr;                         // and their cost in the last launch
     int64_t cond_nw = 0;
@@ -371,6 +383,10 @@ cudaError_t launch_recycle_apply(sdm_ctx *c, uint32_t nz, uint32_t nd);
 cudaError_t launch_moments(sdm_ctx *c, int k);
 cudaError_t launch_sd_conc(sdm_ctx *c);
 cudaError_t launch_cond_ambient(sdm_ctx *c, int what);
+cudaError_t launch_exchange_count(sdm_ctx *c, int leavers, uint32_t *total_host);
+cudaError_t launch_export(sdm_ctx *c, const sdm_sd_block &dst);
+cudaError_t launch_import(sdm_ctx *c, const sdm_sd_block &src, int64_t n);
+cudaError_t launch_block_check(sdm_ctx *c, const sdm_sd_block &src, int64_t n, unsigned *bad_host);
 constexpr int kMaxSpectrumBins = 256;
 // records per tile of the ensemble's radix sort: the histogram table its
 // callers allocate holds 256 counts per tile of this size

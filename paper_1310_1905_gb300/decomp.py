@@ -6,18 +6,19 @@ so a step needs one exchange of the leavers between neighbouring slabs, after
 the transport and before the counting sort.
 
 This module holds that exchange on the host over torch.distributed (gloo or
-nccl): which rank owns a position, the packing of the leavers of every
-attribute into one float64 buffer (multiplicities and ids travel as exact
-integers below 2^53), the swap with the two neighbours and the unpacking.
-Every run here has one GPU, so the library's device path stays one domain
-per GPU (bench.py --gpus N runs replicas); this is the exchange a sharded
-driver would call, tested with two gloo ranks on the CPU.
+nccl): which rank owns a position, the packing of the leavers into two
+blocks (the floating-point attributes as float64, multiplicities and ids as
+int64, so that every integer travels exactly), the swap with the two
+neighbours and the unpacking.  The library's sdm_export_leavers and
+sdm_import move the super-droplets between a context and these blocks.
 """
 from __future__ import annotations
 
 import numpy as np
 
-ATTRS = ("N", "rw2", "rd3", "kappa", "x", "y", "z", "uid")
+FLOATS = ("rw2", "rd3", "kappa", "x", "y", "z")
+INTS = ("N", "uid")
+ATTRS = INTS + FLOATS
 
 
 def slab_of(x: np.ndarray, X: float, world: int) -> np.ndarray:
@@ -26,23 +27,29 @@ def slab_of(x: np.ndarray, X: float, world: int) -> np.ndarray:
     return np.clip(r, 0, world - 1)
 
 
-def pack(state: dict, sel: np.ndarray) -> np.ndarray:
-    """The selected super-droplets as one (n, len(ATTRS)) float64 block;
-    absent attributes travel as zeros."""
+def pack(state: dict, sel: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """The selected super-droplets as an (n, 2) int64 block (N, uid) and an
+    (n, 6) float64 block (r_w^2, r_d^3, kappa, x, y, z); absent attributes
+    travel as zeros.  Multiplicities up to 2^63 - 1 travel exactly."""
     n = int(np.count_nonzero(sel))
-    out = np.zeros((n, len(ATTRS)), np.float64)
-    for k, a in enumerate(ATTRS):
+    ints = np.zeros((n, len(INTS)), np.int64)
+    floats = np.zeros((n, len(FLOATS)), np.float64)
+    for k, a in enumerate(INTS):
         if a in state:
             v = np.asarray(state[a])[sel]
-            if v.dtype.kind in "ui":
-                assert n == 0 or int(v.max()) < 2 ** 53, "integers above 2^53 do not travel exactly as float64"
-            out[:, k] = v
+            assert n == 0 or int(v.max()) < 2 ** 63, "integers must fit int64"
+            ints[:, k] = v.astype(np.int64)
+    for k, a in enumerate(FLOATS):
+        if a in state:
+            floats[:, k] = np.asarray(state[a])[sel]
+    return ints, floats
+
+
+def unpack(ints: np.ndarray, floats: np.ndarray, like: dict) -> dict:
+    """Attributes from packed blocks, in the dtypes of ``like``."""
+    out = {a: ints[:, k].astype(np.asarray(like[a]).dtype) for k, a in enumerate(INTS) if a in like}
+    out.update({a: floats[:, k].astype(np.asarray(like[a]).dtype) for k, a in enumerate(FLOATS) if a in like})
     return out
-
-
-def unpack(block: np.ndarray, like: dict) -> dict:
-    """Attributes from a packed block, in the dtypes of ``like``."""
-    return {a: block[:, k].astype(np.asarray(like[a]).dtype) for k, a in enumerate(ATTRS) if a in like}
 
 
 def concat(a: dict, b: dict) -> dict:
@@ -70,23 +77,25 @@ def exchange(state: dict, X: float, group=None) -> tuple[dict, int, int]:
     recv = []
     for dst, sel in ((left, to_left), (right, to_right)):
         src = right if dst == left else left
-        block = torch.from_numpy(pack(state, sel))
-        n_out = torch.tensor([block.shape[0]], dtype=torch.int64)
+        ints, floats = (torch.from_numpy(b) for b in pack(state, sel))
+        n_out = torch.tensor([ints.shape[0]], dtype=torch.int64)
         n_in = torch.zeros(1, dtype=torch.int64)
         # sizes first, then the blocks; paired send/recv in rank order avoids a deadlock with gloo
         ops = [dist.P2POp(dist.isend, n_out, dst, group), dist.P2POp(dist.irecv, n_in, src, group)]
         for r in dist.batch_isend_irecv(ops):
             r.wait()
-        buf = torch.empty((int(n_in.item()), len(ATTRS)), dtype=torch.float64)
+        m = int(n_in.item())
+        ibuf = torch.empty((m, len(INTS)), dtype=torch.int64)
+        fbuf = torch.empty((m, len(FLOATS)), dtype=torch.float64)
         ops = []
-        if block.shape[0]:
-            ops.append(dist.P2POp(dist.isend, block, dst, group))
-        if buf.shape[0]:
-            ops.append(dist.P2POp(dist.irecv, buf, src, group))
+        if ints.shape[0]:
+            ops += [dist.P2POp(dist.isend, ints, dst, group), dist.P2POp(dist.isend, floats, dst, group)]
+        if m:
+            ops += [dist.P2POp(dist.irecv, ibuf, src, group), dist.P2POp(dist.irecv, fbuf, src, group)]
         for r in dist.batch_isend_irecv(ops) if ops else []:
             r.wait()
-        recv.append(buf.numpy())
+        recv.append((ibuf.numpy(), fbuf.numpy()))
     kept = {k: np.asarray(v)[stay] for k, v in state.items()}
-    for b in recv:
-        kept = concat(kept, unpack(b, state))
-    return kept, int(np.count_nonzero(~stay)), int(sum(b.shape[0] for b in recv))
+    for ib, fb in recv:
+        kept = concat(kept, unpack(ib, fb, state))
+    return kept, int(np.count_nonzero(~stay)), int(sum(ib.shape[0] for ib, _ in recv))

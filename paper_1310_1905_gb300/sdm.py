@@ -30,6 +30,7 @@ INIT = {"lognormal": 0, "exponential": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 BACKEND = {"serial": 0, "openmp": 1, "cuda": 2}
 SOLVER = {"bisect": 0, "fast": 1}
+COND_LAYOUT = {"auto": 0, "fused": 1, "staged": 2}
 ATTR = {"N": 0, "rw2": 1, "rd3": 2, "kappa": 3, "x": 4, "y": 5, "z": 6, "uid": 7}
 ATTR_DTYPE = {"N": np.uint64, "uid": np.uint32}
 
@@ -50,8 +51,14 @@ class sdm_opts_init(C.Structure):
         ("init_dist", C.c_int), ("exp_mean_volume", C.c_double), ("exp_n0", C.c_double),
         ("n_modes", C.c_int), ("modes", C.POINTER(sdm_lognormal)),
         ("seed", C.c_uint64), ("physics", C.c_int), ("precision", C.c_int), ("backend", C.c_int),
-        ("cond_solver", C.c_int),
+        ("cond_solver", C.c_int), ("x_open", C.c_int), ("cond_layout", C.c_int), ("sd_reserve", C.c_int64),
     ]
+
+
+class sdm_sd_block(C.Structure):
+    _fields_ = [("N", C.c_void_p), ("uid", C.c_void_p), ("rw2", C.c_void_p), ("rd3", C.c_void_p),
+                ("kappa", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("on_device", C.c_int)]
 
 
 class sdm_opts(C.Structure):
@@ -88,7 +95,8 @@ SYMBOLS = ["sdm_init", "sdm_destroy", "sdm_last_error", "sdm_step_sync", "sdm_st
            "sdm_euler_step",
            "sdm_diag_rng", "sdm_diag_mom", "sdm_diag_sd_conc", "sdm_diag_ambient", "sdm_diag_spectrum", "sdm_outbuf", "sdm_sizes", "sdm_get_attr",
            "sdm_set_attr", "sdm_get_fields", "sdm_get_step", "sdm_set_step", "sdm_get_stats",
-           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc", "sdm_probe_device"]
+           "sdm_timing_enable", "sdm_get_timing", "sdm_cell_sort", "sdm_cell_sort_noalloc", "sdm_probe_device",
+           "sdm_step_transport", "sdm_step_coalesce", "sdm_export_leavers", "sdm_import"]
 
 
 class sdm_device_peaks(C.Structure):
@@ -140,6 +148,10 @@ def load(build_if_missing: bool = True):
     L.sdm_cell_sort.argtypes = [V, I64, C.c_int32, V, V, V]
     L.sdm_cell_sort_noalloc.argtypes = [V, I64, C.c_int32, V, V, V]
     L.sdm_probe_device.argtypes = [D, P(sdm_device_peaks)]
+    L.sdm_step_transport.argtypes = [ctx, P(sdm_opts)]
+    L.sdm_step_coalesce.argtypes = [ctx, P(sdm_opts)]
+    L.sdm_export_leavers.argtypes = [ctx, sdm_sd_block, I64, P(I64)]
+    L.sdm_import.argtypes = [ctx, sdm_sd_block, I64]
     for s in SYMBOLS:
         if s != "sdm_last_error":
             getattr(L, s).restype = C.c_int
@@ -189,6 +201,9 @@ def make_opts_init(cfg: dict, precision: str = "fp64", backend: str = "cuda"):
     o.precision = PRECISION[precision]
     o.backend = BACKEND[backend]
     o.cond_solver = SOLVER[cfg.get("cond_solver", "fast")]
+    o.x_open = int(cfg.get("x_open", 0))
+    o.cond_layout = COND_LAYOUT[cfg.get("cond_layout", "auto")]
+    o.sd_reserve = int(cfg.get("sd_reserve", 0))
     return o, arr
 
 
@@ -247,6 +262,51 @@ def sdm_step_async(ctx, opts: dict):
     L = load()
     o = make_opts(opts)
     _check(L, ctx, L.sdm_step_async(ctx, C.byref(o)))
+
+
+def sdm_step_transport(ctx, opts: dict):
+    L = load()
+    o = make_opts(opts)
+    _check(L, ctx, L.sdm_step_transport(ctx, C.byref(o)))
+
+
+def sdm_step_coalesce(ctx, opts: dict):
+    L = load()
+    o = make_opts(opts)
+    _check(L, ctx, L.sdm_step_coalesce(ctx, C.byref(o)))
+
+
+BLOCK_FIELDS = (("N", np.uint64), ("uid", np.uint32), ("rw2", np.float64), ("rd3", np.float64),
+                ("kappa", np.float64), ("x", np.float64), ("y", np.float64), ("z", np.float64))
+
+
+def _block(arrays: dict) -> sdm_sd_block:
+    b = sdm_sd_block()
+    for name, _ in BLOCK_FIELDS:
+        a = arrays.get(name)
+        setattr(b, name, None if a is None else a.ctypes.data)
+    b.on_device = 0
+    return b
+
+
+def sdm_export_leavers(ctx, cap: int) -> dict:
+    """The leavers of an x_open context (x outside its domain), host arrays."""
+    L = load()
+    cap = max(1, int(cap))
+    arrays = {name: np.zeros(cap, dt) for name, dt in BLOCK_FIELDS}
+    n = C.c_int64()
+    _check(L, ctx, L.sdm_export_leavers(ctx, _block(arrays), cap, C.byref(n)))
+    return {k: v[:n.value].copy() for k, v in arrays.items()}
+
+
+def sdm_import(ctx, arrays: dict):
+    """Put super-droplets (host arrays as sdm_export_leavers returns them)
+    into free slots."""
+    L = load()
+    n = len(arrays["N"])
+    conv = {name: np.ascontiguousarray(arrays[name], dt) if name in arrays else np.zeros(n, dt)
+            for name, dt in BLOCK_FIELDS}
+    _check(L, ctx, L.sdm_import(ctx, _block(conv), n))
 
 
 def sdm_wait(ctx, timeout_s: float = -1.0) -> float:
@@ -419,6 +479,18 @@ class Particles:
 
     def step_async(self, opts):
         sdm_step_async(self.ctx, opts)
+
+    def step_transport(self, opts):
+        sdm_step_transport(self.ctx, opts)
+
+    def step_coalesce(self, opts):
+        sdm_step_coalesce(self.ctx, opts)
+
+    def export_leavers(self, cap=None):
+        return sdm_export_leavers(self.ctx, self.n_sd if cap is None else cap)
+
+    def import_(self, arrays: dict):
+        sdm_import(self.ctx, arrays)
 
     def euler_step(self, th, rv, rhoCx=None, rhoCy=None, rhoCz=None, th0=None, rv0=None, advect=True):
         sdm_euler_step(self.ctx, th, rv, rhoCx, rhoCy, rhoCz, th0, rv0, advect)

@@ -24,7 +24,8 @@ def _free_port() -> int:
 
 def global_state(seed=0):
     rng = np.random.default_rng(seed)
-    return dict(N=rng.integers(1, 2 ** 50, N_SD, dtype=np.int64).astype(np.uint64),
+    # multiplicities up to 2^62: above 2^53 they would not travel exactly as float64
+    return dict(N=rng.integers(1, 2 ** 62, N_SD, dtype=np.int64).astype(np.uint64),
                 rw2=rng.uniform(1e-14, 1e-8, N_SD), rd3=rng.uniform(1e-24, 1e-21, N_SD),
                 kappa=np.full(N_SD, 0.61), x=rng.uniform(0, X, N_SD), z=rng.uniform(0, Z, N_SD),
                 uid=np.arange(N_SD, dtype=np.uint32))
