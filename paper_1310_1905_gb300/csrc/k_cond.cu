@@ -91,7 +91,8 @@ SDM_HD float fs_f(float Kn) {
 enum { kDgNone = 0, kDgKoehler = 1, kDgFull = 2 };
 
 template <int DG>
-SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int physics, float *err, float *dgdx) {
+SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int physics, float *err, float *dgdx,
+                      float *edg = nullptr, float *curv = nullptr, float *mag = nullptr) {
     const float r = sqrtf(x);
     const float r3 = x * r;
     const float num = r3 - rd3, den = r3 - rd3 * (1.0f - kappa);
@@ -146,13 +147,30 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
         const float wD = Deff / D;
         const float dlnc = wD * dlnD + (1.0f - wD) * dlnK;
         *dgdx = (g * dlnc - c * drho_dr * r) / (2.0f * x);
+        if (DG == kDgFull && edg) {
+            // an absolute bound of dg/dx's error: g carries err; the Koehler
+            // slope's two terms, D_eff's logarithmic derivatives and the
+            // factor c each carry a few tens of FP32 ulps (2^-16 covers them
+            // with room)
+            const float mk = t.rho_vs * kel * (3.0f * kappa * fdiv(rd3, den) * fdiv(x, den) + aw * fdiv(t.A, x));
+            *edg = (*err * fabsf(dlnc) +
+                    1.52587890625e-5f * (fabsf(g) * (fabsf(dlnc) + fabsf(dlnD) + fabsf(dlnK) + 1.0f) + c * mk * r)) /
+                   (2.0f * x);
+            // x^2 |g''| bounded from the scales on which the Koehler factor
+            // varies: ln a_w by up to 1.5 amp, the Kelvin factor by A/r, the
+            // D_eff factor by O(1), per unit ln x
+            const float sc = 2.0f + 1.5f * amp + Ar;
+            *curv = c * (2.0f * fabsf(t.rho_v_eff - rho_o) + rho_o * sc * sc) / (x * x);
+            *mag = c * (t.rho_v_eff + rho_o);  // the size of the terms whose difference g is
+        }
     }
     return g;
 }
 
 struct SolveCounters {
     int euler, fallback;
-    int evals;  // FP64 growth evaluations of the fast solve: the cost measure of the launch order
+    int evals;      // FP64 growth evaluations of the fast solve: the cost measure of the launch order
+    int certified;  // solves settled by a certified Newton step (staged layout)
 };
 
 // The growth rate of eq. (maxmason) rearranged for FP64 throughput: with
@@ -213,16 +231,19 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
     return Coef{2.0 * a * b, rho_w * (b * DM + t.Dterm * a * DT)};
 }
 
-// The FP32 growth rate with its error bound and dg/dx.
+// The FP32 growth rate with its error bound and dg/dx; with BOUNDS also
+// dg/dx's error bound edg, a bound curv of |d2g/dx2| and the size mag of the
+// terms whose difference g is.
 struct GF {
-    float g, err, dg;
+    float g, err, dg, edg, curv, mag;
 };
 
-template <int DG>
+template <int DG, bool BOUNDS = false>
 SDM_HD GF growth_f3(float x, float rd3, float kappa, const ThermoF &t, int physics) {
     GF r;
-    r.dg = 0.0f;
-    r.g = growth_f<DG>(x, rd3, kappa, t, physics, &r.err, &r.dg);
+    r.dg = r.edg = r.curv = r.mag = 0.0f;
+    if (BOUNDS) r.g = growth_f<DG>(x, rd3, kappa, t, physics, &r.err, &r.dg, &r.edg, &r.curv, &r.mag);
+    else r.g = growth_f<DG>(x, rd3, kappa, t, physics, &r.err, &r.dg);
     return r;
 }
 
@@ -238,6 +259,16 @@ SDM_HD __noinline__ GF growth_f3_full(float x, float rd3, float kappa, const The
     return growth_f3<kDgFull>(x, rd3, kappa, *t, physics);
 }
 
+SDM_HD __noinline__ GF growth_f3_bounds(float x, float rd3, float kappa, const ThermoF *t, int physics) {
+    return growth_f3<kDgFull, true>(x, rd3, kappa, *t, physics);
+}
+
+// the full FP32 growth rate, with the slope's bounds for a certified solve
+template <bool CERT>
+SDM_HD GF growth_f3_slope(float x, float rd3, float kappa, const ThermoF *t, int physics) {
+    return CERT ? growth_f3_bounds(x, rd3, kappa, t, physics) : growth_f3_full(x, rd3, kappa, t, physics);
+}
+
 // the FP64 residual with the term-by-term growth rate, on the rare paths
 // (undecided bracket ends, replay decisions, the bisection fallback)
 SDM_HD __noinline__ double fres_rare(double x, double x0, double rd3, double kappa, const Thermo *t,
@@ -251,6 +282,7 @@ struct FastSolve {
     double x0, rd3, kappa;
     double a, b, lo, hi, xk, xp, fp, slope, sdx, sdf, x1;
     double rd2;  // r_d^2 when the bracket's lower end is clamped to it
+    double es, cv, xsp;  // certified solves: the FP32 slope's error bound, a bound of |f''|, its point
     float Lu, Hu, mu;
     int k;
     bool plo, undecided, mu_inside, pmu, have_slope, clamp;
@@ -308,7 +340,9 @@ SDM_HD __noinline__ double bisect_rest(double lo, double hi, bool plo, double x0
 // 1. locate: from the bracket [x0 + L, x0 + H] (FP32 increments) whose ends
 //    have the signs plo and !plo, halve in FP32 while FP32 decides - the
 //    halves the FP64 bisection takes, up to FP32 rounding of the midpoints -
-//    and set up the polish at the point mu where it stops deciding.
+//    and set up the polish at the point mu where it stops deciding.  CERT:
+//    also the bounds a certified Newton step needs (newton_certified).
+template <bool CERT>
 SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &tf, double dtp, int physics) {
     const double x0 = S.x0;
     const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
@@ -334,7 +368,14 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
     if (!undecided) mu = 0.5f * (L + H);
     S.mu = mu;
     // f' at mu for the first Newton step (D_eff's variation included)
-    const float dg = growth_f3_full(x0f + mu, rd3f, kf, &tf, physics).dg;
+    const float xs = x0f + mu;
+    const GF qs = growth_f3_slope<CERT>(xs, rd3f, kf, &tf, physics);
+    const float dg = qs.dg;
+    if (CERT) {
+        S.es = dtp * (double)qs.edg;
+        S.cv = dtp * (double)qs.curv;
+        S.xsp = (double)xs;
+    }
     // 2. the polish starts at mu inside [lo, hi]
     double lo = x0 + (double)L, hi = x0 + (double)H;
     if (!(lo >= S.a)) lo = S.a;
@@ -353,8 +394,26 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
     S.k = 0;
 }
 
+// A Newton step xn = xb - f(xb)/s with the FP32 slope s, f(xb) known to
+// +-efb: between xb and the root f' differs from s by at most
+// ds = es + cv (|xsp - xb| + 2 |xn - xb|), so (mean value theorem) the root
+// lies within (|xn - xb| ds + efb) / (|s| - ds) of xn.  Certified when that
+// is below 2^-43 xn (1.1e-13 of it, nearly nine times inside the 1e-12 bar).
+SDM_HD bool newton_certified(const FastSolve &S, double xb, double xn, double efb) {
+    const double step = fabs(xn - xb), as = fabs(S.slope);
+    const double ds = S.es + S.cv * (fabs(S.xsp - xb) + 2.0 * step);
+    if (!(ds < 0.25 * as)) return false;
+    return (step * ds + efb) / (as - ds) <= 0x1p-43 * xn;
+}
+
+// fs_replay is defined below; a certified step from x0 replays the halvings.
+SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                        SolveCounters &cnt);
+
 // After g0 = g(x0) in FP64: the paper's bracket and Euler test exactly, then
-// the locate.  Returns true when the solve is finished (S.x1 set).
+// the locate.  Returns true when the solve is finished (S.x1 set).  CERT: a
+// certified Newton step from x0 finishes it too.
+template <bool CERT>
 SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
                         SolveCounters &cnt) {
     const double x0 = S.x0;
@@ -366,12 +425,37 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     // the ends' signs; at x0 itself f = -dtp g0 exactly.  The sign of f at
     // x0 + d (d an FP32 increment) is computed in FP32 and trusted where |f|
     // exceeds its error bound (it is then the sign an FP64 evaluation gives).
+    // CERT: first from the FP32 slope at x0.  With D = xe - x0 (exact: xe is
+    // within x0/16 of x0), f(xe) = D - dt' g0 - dt' g'(xi) D for some xi
+    // between them, and g'(xi) lies within B = edg + curv (|D| + |x0 - x0f|)
+    // of the FP32 slope dg; the sign is taken where the linear value clears
+    // that, its own rounding and the rounding of an FP64 evaluation of f
+    // (2^-46 of the terms' size mag).  Near equilibrium g0 is too small for
+    // FP32 to sign f at either end, and this saves the FP64 evaluation there.
+    GF q0;
+    if (CERT) q0 = growth_f3_slope<CERT>(x0f, rd3f, kf, &tf, physics);
     bool pe[2];
     for (int e = 0; e < 2; ++e) {
         const double xe = e ? b : a;
         if (xe == x0) {
             pe[e] = -dtp * g0 > 0.0;
-        } else {
+            continue;
+        }
+        if (CERT) {
+            const double D = xe - x0;
+            if (fabs(D) <= 0.0625 * x0) {
+                const double lin = dtp * (double)q0.dg * D;
+                const double F = (D - dtp * g0) - lin;
+                const double B = (double)q0.edg + (double)q0.curv * (fabs(D) + fabs(x0 - (double)x0f));
+                const double M = dtp * B * fabs(D) + 0x1p-48 * (fabs(D) + dtp * fabs(g0) + fabs(lin)) +
+                                 0x1p-46 * dtp * (double)q0.mag;
+                if (fabs(F) > M) {
+                    pe[e] = F > 0.0;
+                    continue;
+                }
+            }
+        }
+        {
             const float d = (float)(xe - x0);
             const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
             const float f = d - dtpf * q.g;
@@ -405,16 +489,31 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     S.pmu = false;
     S.lo = a;
     S.hi = b;
-    const float dg = growth_f3_full(x0f, rd3f, kf, &tf, physics).dg;
-    S.slope = 1.0 - dtp * (double)dg;
+    if (!CERT) q0 = growth_f3_slope<CERT>(x0f, rd3f, kf, &tf, physics);
+    S.slope = 1.0 - dtp * (double)q0.dg;
     S.have_slope = true;
     S.sdx = S.sdf = 1.0;
     const double f0 = -dtp * g0;
     double xk = S.slope > 0.0 ? x0 - f0 / S.slope : 0.5 * (a + b);
-    if (!(xk > a && xk < b)) xk = 0.5 * (a + b);
+    const bool newton = xk > a && xk < b;
+    if (!newton) xk = 0.5 * (a + b);
     S.xp = S.fp = 0.0;
     S.xk = xk;
     S.k = 0;
+    if (CERT) {
+        // the Newton step from x0 is the result where its certified error is
+        // far below 1e-12: f(x0) is known to the rounding of g0's terms, at
+        // most 2^-47 of their size mag; the replay then checks that the
+        // bisection's halvings lead to it
+        S.es = dtp * (double)q0.edg;
+        S.cv = dtp * (double)q0.curv;
+        S.xsp = x0;
+        if (newton && newton_certified(S, x0, xk, 0x1p-47 * dtp * (double)q0.mag)) {
+            cnt.certified++;
+            S.x1 = fs_replay(S, xk, t, tf, dtp, physics, cnt);
+            return true;
+        }
+    }
     return false;
 }
 
@@ -431,6 +530,7 @@ enum { kStartPolish = 0, kStartEuler = 1, kStartTiny = 2, kStartExact = 3 };
 // FP32 bound plus |f'| u, so every decision taken here is the one the FP64
 // bracket gives.  Only the Euler step, whose result is g(x0) itself, then
 // needs g(x0) in FP64: the other solves save that evaluation.
+template <bool CERT>
 SDM_HD int fs_start(FastSolve &S, const ThermoF &tf, double dtp, int physics) {
     const double x0 = S.x0;
     const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
@@ -487,7 +587,7 @@ SDM_HD int fs_start(FastSolve &S, const ThermoF &tf, double dtp, int physics) {
     const double w = (double)(H - L), uw = S.clamp ? 0.0 : (double)u;
     if (w + uw <= 0x1p-52 * (S.b - uw)) return kStartTiny;
     if (!(w - uw > 0x1p-52 * (S.b + uw))) return kStartExact;
-    fs_locate(S, L, H, pa, tf, dtp, physics);
+    fs_locate<CERT>(S, L, H, pa, tf, dtp, physics);
     return kStartPolish;
 }
 
@@ -552,7 +652,9 @@ SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &
 
 // After v = growth_eval(S.xk, false, .., &mag): one polish step (bracketed
 // Newton, then secant, in FP64 with exact signs).  Returns true when the solve is
-// finished (S.x1 set).
+// finished (S.x1 set).  CERT: the first Newton step also settles where it is
+// certified (newton_certified).
+template <bool CERT>
 SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t, const ThermoF &tf, double dtp,
                             int physics, SolveCounters &cnt) {
     const double xk = S.xk, fk = xk - S.x0 - dtp * v;
@@ -593,7 +695,13 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t,
         // f(xk) is at the rounding level of its evaluation: near it a secant
         // slope from close points is itself rounding.
         const bool inside = at_noise ? xn >= lo && xn <= hi : xn > lo && xn < hi;
-        if (fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk && inside) {
+        // certified: f(xk) carries the rounding of the one-division form, at
+        // most 2^-47 of its terms
+        const bool small = fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk;
+        const bool cert = CERT && !small && !secant && S.have_slope &&
+                          newton_certified(S, xk, xn, 0x1p-47 * (fabs(xk - S.x0) + dtp * mag));
+        if (inside && (small || cert)) {
+            if (cert) cnt.certified++;
             r = xn;
             settled = true;
         } else {
@@ -618,6 +726,7 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t,
 }
 
 // the whole fast solve for one super-droplet
+template <bool CERT = false>
 __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, const Thermo &t,
                                           const ThermoF &tf, double dtp, int physics, SolveCounters &cnt) {
     FastSolve S;
@@ -627,7 +736,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
     // The first FP64 evaluation is g(x0) where the start needs it (an Euler
     // step, or FP32 could not decide), else the polish's first; then one per
     // polish step, all through one call site.
-    const int start = fs_start(S, tf, dtp, physics);
+    const int start = fs_start<CERT>(S, tf, dtp, physics);
     for (int k = 0; k < 15; ++k) {
         const bool g0 = k == 0 && start != kStartPolish;
         cnt.evals++;
@@ -635,13 +744,13 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         const double v = growth_eval(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
         if (g0) {
             if (start == kStartExact) {
-                if (fs_after_g0(S, v, t, tf, dtp, physics, cnt)) return S.x1;
+                if (fs_after_g0<CERT>(S, v, t, tf, dtp, physics, cnt)) return S.x1;
                 continue;
             }
             if (start == kStartEuler) cnt.euler++;
             return fs_euler(S, v, dtp);
         }
-        if (fs_after_polish(S, v, mag, t, tf, dtp, physics, cnt)) return S.x1;
+        if (fs_after_polish<CERT>(S, v, mag, t, tf, dtp, physics, cnt)) return S.x1;
     }
     return S.x1;  // not reached: the polish finishes within 13 evaluations
 }
@@ -785,7 +894,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_condense(SdArrays s, const uint32
     double thc = live ? th[c] : 289.0, rvc = live ? rv[c] : 0.0;
     const double rd = live ? rhod[c] : 1.0;
     const double dtp = g.dt / sstp;
-    SolveCounters cnt{0, 0, 0};
+    SolveCounters cnt{0, 0, 0, 0};
     bool bad = false;
     // the cell's ambient state for the solves sits in shared memory: read
     // there by reference it takes no registers across the solve
@@ -963,7 +1072,7 @@ __global__ void k_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t 
     const Thermo &t = s_t;
     const ThermoF &tf = s_tf;
     const double dtp = p.dt / p.sstp;
-    SolveCounters cnt{0, 0, 0};
+    SolveCounters cnt{0, 0, 0, 0};
     double sum = 0.0;
     bool bad = false;
     for (uint32_t i = tile_beg[tile] + threadIdx.x; i < tile_end[tile]; i += blockDim.x) {
@@ -1105,50 +1214,74 @@ __global__ void k_cs_cells(const double *th, const double *rv, const double *rho
 
 // one warp per cell: every super-droplet's FP32 start; the record at its
 // storage index (round 0 takes every index)
+// The records go to one list of n slots: those whose first FP64 evaluation
+// is g(x0) from the front (count n_g0), those that start their polish from
+// the back (count n_pol), so that round 0 runs each kind in warps of its own.
 __global__ void k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells, double dtp,
-                           int physics, StagedRec *rec, double *x1, unsigned *count0, unsigned n_sd) {
+                           int physics, StagedRec *rec, double *x1, unsigned *n_g0, unsigned *n_pol,
+                           unsigned n_sd) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (c64 == 0 && threadIdx.x == 0) *count0 = n_sd;  // round 0 takes every record
-    if (c64 >= n_cells) return;
     const int c = (int)c64, lane = threadIdx.x & 31;
-    const ThermoF &tf = cells[c].tf;
-    for (uint32_t i = offset[c] + lane; i < offset[c + 1]; i += 32) {
-        StagedRec &r = rec[i];
-        r.sd = i;
-        const double x0 = s.rw2[i];
-        if (s.N[i] == 0) {
-            r.task = kTaskNone;
-            x1[i] = x0;
-            continue;
-        }
+    const bool live = c64 < n_cells;
+    const uint32_t beg = live ? offset[c] : 0, end = live ? offset[c + 1] : 0;
+    const ThermoF &tf = cells[live ? c : 0].tf;
+    // the cell's super-droplets in rounds of 32 (a warp is one cell, so every
+    // lane takes the same trips and takes part in the ballots)
+    for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        int task = kTaskNone;
         FastSolve S;
-        S.x0 = x0;
-        S.rd3 = s.rd3[i];
-        S.kappa = s.kappa[i];
-        const int st = fs_start(S, tf, dtp, physics);
-        r.task = st == kStartPolish  ? kTaskPolish
-                 : st == kStartExact ? kTaskG0Exact
-                 : st == kStartEuler ? kTaskG0Euler
-                                     : kTaskG0Tiny;
-        r.S = S;
+        if (i < end) {
+            const double x0 = s.rw2[i];
+            if (s.N[i] == 0) {
+                x1[i] = x0;
+            } else {
+                S.x0 = x0;
+                S.rd3 = s.rd3[i];
+                S.kappa = s.kappa[i];
+                const int st = fs_start<true>(S, tf, dtp, physics);
+                task = st == kStartPolish  ? kTaskPolish
+                       : st == kStartExact ? kTaskG0Exact
+                       : st == kStartEuler ? kTaskG0Euler
+                                           : kTaskG0Tiny;
+            }
+        }
+        const unsigned mg = __ballot_sync(0xffffffffu, task != kTaskNone && task != kTaskPolish);
+        const unsigned mp = __ballot_sync(0xffffffffu, task == kTaskPolish);
+        unsigned bg = 0, bp = 0;
+        if (lane == 0) {
+            if (mg) bg = atomicAdd(n_g0, (unsigned)__popc(mg));
+            if (mp) bp = atomicAdd(n_pol, (unsigned)__popc(mp));
+        }
+        bg = __shfl_sync(0xffffffffu, bg, 0);
+        bp = __shfl_sync(0xffffffffu, bp, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (task != kTaskNone) {
+            const unsigned pos = task == kTaskPolish ? n_sd - 1u - (bp + __popc(mp & below)) : bg + __popc(mg & below);
+            StagedRec &r = rec[pos];
+            r.sd = i;
+            r.task = task;
+            r.S = S;
+        }
     }
 }
 
 // one FP64 growth evaluation per record; the records that need another go
 // to the next list (one atomic per block), the finished write r_w^2
-__global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, StagedRec *out,
-                                                 unsigned *n_out, const uint32_t *cell_of_sd, const StagedCell *cells,
-                                                 double dtp, int physics, double *x1, DevStats *st) {
+__global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, int64_t rev_end,
+                                                 StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
+                                                 const StagedCell *cells, double dtp, int physics, double *x1,
+                                                 DevStats *st) {
     __shared__ unsigned s_warp[8], s_base;
     const unsigned n = *n_in;
-    SolveCounters cnt{0, 0, 0};
+    SolveCounters cnt{0, 0, 0, 0};
     bool bad = false;
     for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const unsigned t = base + threadIdx.x;
         bool keep = false;
         StagedRec r;
         if (t < n) {
-            r = in[t];
+            r = rev_end ? in[rev_end - 1 - t] : in[t];  // rev_end: records stored from the back
             if (r.task != kTaskNone) {
                 const StagedCell &cl = cells[cell_of_sd[r.sd]];
                 FastSolve &S = r.S;
@@ -1162,9 +1295,9 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                     S.x1 = fs_euler(S, v, dtp);
                     done = true;
                 } else if (r.task == kTaskG0Exact) {
-                    done = fs_after_g0(S, v, cl.t, cl.tf, dtp, physics, cnt);
+                    done = fs_after_g0<true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
                 } else {
-                    done = fs_after_polish(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
+                    done = fs_after_polish<true>(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
                 }
                 if (done) {
                     x1[r.sd] = S.x1;
@@ -1243,7 +1376,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_rec[1], sizeof(StagedRec) * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_cell, sizeof(StagedCell) * (size_t)nc + 4 * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_x1, 8 * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedRounds + 2));
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedRounds + 3));
         if (e != cudaSuccess) return e;
     }
     StagedRec *rec[2] = {(StagedRec *)c->cs_rec[0], (StagedRec *)c->cs_rec[1]};
@@ -1259,16 +1392,22 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
     const int eval_blocks = n_sm * 8;
     for (int sub = 0; sub < o.sstp_cond; ++sub) {
         k_cs_cells<<<grid_for(nc, 128), 128, 0, c->stream>>>(c->th, c->rv, c->rhod, nc, o.RH_max, cells);
-        // round 0 takes every record (count n); each round's survivors feed the next
-        e = cudaMemsetAsync(c->cs_cnt, 0, 4 * (kStagedRounds + 2), c->stream);
+        // round 0 in two launches, the g(x0) records (front of the list) and
+        // the polish records (back); each round's survivors feed the next
+        unsigned *cnt = c->cs_cnt, *n_pol = c->cs_cnt + kStagedRounds + 2;
+        e = cudaMemsetAsync(cnt, 0, 4 * (kStagedRounds + 3), c->stream);
         if (e != cudaSuccess) return e;
         k_cs_start<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, dtp,
-                                                                   c->oi.physics, rec[0], c->cs_x1, c->cs_cnt,
+                                                                   c->oi.physics, rec[0], c->cs_x1, cnt, n_pol,
                                                                    (unsigned)n);
-        for (int r = 0; r < kStagedRounds; ++r)
-            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], c->cs_cnt + r, rec[(r + 1) & 1],
-                                                          c->cs_cnt + r + 1, cell_of_sd, cells, dtp, c->oi.physics,
-                                                          c->cs_x1, c->dstats);
+        for (int part = 0; part < 2; ++part)
+            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0, rec[1], cnt + 1,
+                                                          cell_of_sd, cells, dtp, c->oi.physics, c->cs_x1,
+                                                          c->dstats);
+        for (int r = 1; r < kStagedRounds; ++r)
+            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1], cnt + r + 1,
+                                                          cell_of_sd, cells, dtp, c->oi.physics, c->cs_x1,
+                                                          c->dstats);
         k_cs_update<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, c->cs_x1,
                                                                     c->th, c->rv, c->rhod, c->grid.dV, c->dstats);
     }

@@ -56,10 +56,10 @@ def solve(x0, rd3, kappa, cell, th, rv, rhod, dtp, solver=1, RH_max=44.0, physic
     x0, rd3, kappa, th, rv, rhod = _prep(x0, rd3, kappa, th, rv, rhod)
     cell = np.ascontiguousarray(cell, np.int64)
     out = np.empty_like(x0)
-    cnt = np.zeros(3, np.int64)
+    cnt = np.zeros(4, np.int64)
     lib().hc_solve(len(x0), _d(x0), _d(rd3), _d(kappa), cell.ctypes.data_as(C.POINTER(C.c_int64)), _d(th), _d(rv),
                    _d(rhod), RH_max, dtp, physics, solver, _d(out), cnt.ctypes.data_as(C.POINTER(C.c_int64)))
-    return out, dict(euler=int(cnt[0]), fallback=int(cnt[1]), evals=int(cnt[2]))
+    return out, dict(euler=int(cnt[0]), fallback=int(cnt[1]), evals=int(cnt[2]), certified=int(cnt[3]))
 
 
 def growth(x, rd3, kappa, cell, th, rv, rhod, RH_max=44.0, physics=1):

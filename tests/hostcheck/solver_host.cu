@@ -15,12 +15,14 @@ Thermo cell_thermo(int64_t c, const double *th, const double *rv, const double *
 }  // namespace
 
 // solver: 0 the bisection (SDM_SOLVER_BISECT), 1 the fast solve
-// (SDM_SOLVER_FAST), 2 the FP32 solve of the mixed mode.  counters: Euler
-// steps, exact-bisection fallbacks, FP64 growth evaluations.
+// (SDM_SOLVER_FAST), 2 the FP32 solve of the mixed mode, 3 the fast solve
+// with certified Newton steps (the staged layout's).  counters: Euler
+// steps, exact-bisection fallbacks, FP64 growth evaluations, certified
+// settles.
 extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const double *kappa, const int64_t *cell,
                          const double *th, const double *rv, const double *rhod, double RH_max, double dtp,
                          int physics, int solver, double *x1, int64_t *counters) {
-    SolveCounters cnt{0, 0, 0};
+    SolveCounters cnt{0, 0, 0, 0};
     for (int64_t q = 0; q < n; ++q) {
         const Thermo t = cell_thermo(cell[q], th, rv, rhod, RH_max);
         const ThermoF tf = to_float(t);
@@ -29,7 +31,9 @@ extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const d
             x1[q] = solve_rw2_bisect(x0[q], rd3[q], kappa[q], t, dtp, physics, &eu);
             cnt.euler += eu;
         } else if (solver == 1) {
-            x1[q] = solve_rw2_fast(x0[q], rd3[q], kappa[q], t, tf, dtp, physics, cnt);
+            x1[q] = solve_rw2_fast<false>(x0[q], rd3[q], kappa[q], t, tf, dtp, physics, cnt);
+        } else if (solver == 3) {
+            x1[q] = solve_rw2_fast<true>(x0[q], rd3[q], kappa[q], t, tf, dtp, physics, cnt);
         } else {
             solve_rw2_f32(x0[q], rd3[q], kappa[q], tf, (float)dtp, physics, &x1[q], cnt);
         }
@@ -37,6 +41,7 @@ extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const d
     counters[0] = cnt.euler;
     counters[1] = cnt.fallback;
     counters[2] = cnt.evals;
+    counters[3] = cnt.certified;
 }
 
 // The FP32 growth rate with its error bound, and the FP64 one, at x.

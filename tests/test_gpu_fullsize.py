@@ -209,14 +209,17 @@ def test_full_size_spectrum(name):
         assert_close(f"spectrum of cell {c}", spec[:, c], ref, atol=1e-300)
 
 
+@pytest.mark.parametrize("layout", ["fused", "staged"])
 @pytest.mark.parametrize("name,steps", [("icmw_2d", 10), ("updraft_3d", 2)])
-def test_full_domain_fast_solve_is_the_bisection(name, steps):
+def test_full_domain_fast_solve_is_the_bisection(name, steps, layout):
     """Every droplet of the full domain: the fast solver (SDM_SOLVER_FAST,
-    the bench's) against the device's own implementation of the paper's
-    bisection (SDM_SOLVER_BISECT, which the small-case tests check against
-    the oracle), from the same state, step after step: both take the same
-    device thermodynamics, so they must agree within 1e-12 everywhere."""
+    the bench's) in both condensation layouts against the device's own
+    implementation of the paper's bisection (SDM_SOLVER_BISECT, which the
+    small-case tests check against the oracle), from the same state, step
+    after step: both take the same device thermodynamics, so they must
+    agree within 1e-12 everywhere."""
     w = workload(name)
+    w.cfg["cond_layout"] = layout
     fast = gpu_particles(w)
     bis = sdm.Particles(dict(w.cfg, cond_solver="bisect"), w.th, w.rv, w.rhod, w.rhoCx, w.rhoCy, w.rhoCz)
     th, rv = np.ascontiguousarray(w.th).copy(), np.ascontiguousarray(w.rv).copy()
@@ -234,4 +237,4 @@ def test_full_domain_fast_solve_is_the_bisection(name, steps):
         assert (rel <= RTOL).all(), f"{(rel > RTOL).sum()} of {rel.size} beyond 1e-12, worst {rel.max():.3e}"
         assert_close("theta", th, th_b)
         assert_close("r_v", rv, rv_b)
-    print(f"{name}: {w.n_sd} droplets x {steps} steps, worst fast-bisection difference {worst:.3e}")
+    print(f"{name} ({layout}): {w.n_sd} droplets x {steps} steps, worst fast-bisection difference {worst:.3e}")

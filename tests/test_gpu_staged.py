@@ -1,10 +1,10 @@
 """The staged condensation (cond_layout = staged: per substep FP32 starts,
 rounds of FP64 growth evaluations over compacted lists, then the cell sums)
-against the fused kernel and the oracle.  Each super-droplet's solve takes
-the same steps in both layouts; the compiler may contract products into
-fused multiply-adds differently in the two kernels, and the cell sums add
-in another order, so the layouts agree within 1e-12, and each matches the
-oracle within 1e-12."""
+against the fused kernel and the oracle.  The staged solve also settles on
+a Newton step whose certified error is below 2^-43 x, where the fused one
+takes one more polish step; both stay within 1e-12 of the bisection's root,
+so the layouts agree within 2e-12 (the cell sums also add in another
+order), and each matches the oracle within 1e-12."""
 import numpy as np
 import pytest
 
@@ -34,9 +34,11 @@ def test_staged_matches_fused_2d():
     b, thb, rvb = run(w, "staged", 5, ALL)
     sa, sb = a.state(), b.state()
     assert np.array_equal(sa["N"], sb["N"])
-    np.testing.assert_allclose(sb["rw2"], sa["rw2"], rtol=1e-12, atol=0)
-    for k in ("rd3", "kappa", "x", "z"):
+    np.testing.assert_allclose(sb["rw2"], sa["rw2"], rtol=2e-12, atol=0)
+    for k in ("rd3", "kappa", "x"):
         assert np.array_equal(sa[k], sb[k]), k
+    # the fall speed follows r_w: z moves by the rounding-level difference
+    np.testing.assert_allclose(sb["z"], sa["z"], rtol=1e-12, atol=1e-9)
     np.testing.assert_allclose(thb, tha, rtol=1e-13)
     np.testing.assert_allclose(rvb, rva, rtol=1e-12)
     print("2D staged vs fused: worst rel rw2", np.max(np.abs(sb["rw2"] - sa["rw2"]) / sa["rw2"]),
@@ -49,7 +51,7 @@ def test_staged_matches_fused_3d():
     b, thb, rvb = run(w, "staged", 3, ALL)
     sa, sb = a.state(), b.state()
     assert np.array_equal(sa["N"], sb["N"])
-    np.testing.assert_allclose(sb["rw2"], sa["rw2"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(sb["rw2"], sa["rw2"], rtol=2e-12, atol=0)
     np.testing.assert_allclose(thb, tha, rtol=1e-13)
     np.testing.assert_allclose(rvb, rva, rtol=1e-12)
 

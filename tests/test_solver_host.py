@@ -49,21 +49,27 @@ def states():
     return list(trajectory())
 
 
-def test_fast_solve_is_the_bisection_within_1e12(states):
-    n = worst = fallbacks = evals = 0
+@pytest.mark.parametrize("solver", [1, 3], ids=["fast", "certified"])
+def test_fast_solve_is_the_bisection_within_1e12(states, solver):
+    """Both forms of the fast solve: the fused kernel's, and the staged
+    layout's, which also settles on a Newton step whose error bound (from
+    the FP32 slope's error and curvature bounds) is below 2^-43 x."""
+    n = worst = fallbacks = evals = certified = 0
     for args in states:
         ref = oracle.solve_batch(*args)
-        got, c = hostcheck.solve(*args, solver=1)
+        got, c = hostcheck.solve(*args, solver=solver)
         rel = np.abs(got - ref) / ref
         assert (rel <= 1e-12).all(), f"{(rel > 1e-12).sum()} solves differ by more than 1e-12; worst {rel.max():.3e}"
         n += len(ref)
         worst = max(worst, rel.max())
         fallbacks += c["fallback"]
         evals += c["evals"]
+        certified += c["certified"]
     print(f"{n} solves, worst relative difference {worst:.2e}, {fallbacks} exact fallbacks, "
-          f"{evals / n:.3f} FP64 growth evaluations per solve")
+          f"{evals / n:.3f} FP64 growth evaluations per solve, {certified} certified settles")
     assert n > 400_000
     assert evals / n < 2.5  # against about 50 for the bisection
+    assert (certified > n // 100) == (solver == 3)
 
 
 def test_host_bisection_is_the_oracle_bisection(states):
