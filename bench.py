@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cells", type=int, default=128, help="updraft_3d: cells per dimension")
+    ap.add_argument("--nz", type=int, default=None,
+                    help="updraft_3d: levels, when they differ from --cells (a profile of fewer columns of the "
+                         "full-height domain)")
     ap.add_argument("--cond-layout", default="auto", choices=["auto", "fused", "staged"],
                     help="condensation kernels: fused, staged, or chosen by domain size")
     ap.add_argument("--profile-one-step", action="store_true",
@@ -107,11 +110,11 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name: str, seed: int, cells: int = 128, cond_layout: str = "auto"):
+def make_workload(name: str, seed: int, cells: int = 128, cond_layout: str = "auto", nz: int | None = None):
     if name == "icmw_2d":
         w = workloads.icmw_2d(seed=seed)
     elif name == "updraft_3d":
-        w = workloads.updraft_3d(nx=cells, ny=cells, nz=cells, seed=seed)
+        w = workloads.updraft_3d(nx=cells, ny=cells, nz=nz or cells, seed=seed)
     else:
         w = workloads.golovin_box(seed=seed)
     w.cfg["cond_layout"] = cond_layout
@@ -187,7 +190,7 @@ def run_gpu(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    w = make_workload(args.workload, seed=rank, cells=args.cells, cond_layout=args.cond_layout)
+    w = make_workload(args.workload, seed=rank, cells=args.cells, cond_layout=args.cond_layout, nz=args.nz)
     opts = w.opts
     if args.workload == "golovin_box":
         opts = dict(w.opts)

@@ -94,12 +94,15 @@ enum { SDM_COND_AUTO = 0, SDM_COND_FUSED = 1, SDM_COND_STAGED = 2 };
  *   same bracket, the same midpoints and the same sign decisions, decided in
  *   FP32 where an error bound proves the sign, then finishes with a
  *   bracketed FP64 Newton/secant iteration to the same sign change.
- * cond_layout: how the fast FP64 condensation runs on the GPU, with the same
- *   result per super-droplet: SDM_COND_FUSED, one kernel per step carrying
- *   every solve; SDM_COND_STAGED, per substep a chain of small kernels (FP32
- *   starts, rounds of FP64 evaluations over compacted lists, the cell
- *   sums); SDM_COND_AUTO (0) picks by domain size.  Other solvers and the
- *   mixed mode always run fused.
+ * cond_layout: how the fast FP64 condensation runs on the GPU:
+ *   SDM_COND_FUSED, one kernel per step carrying every solve;
+ *   SDM_COND_STAGED, per substep a chain of small kernels (FP32 starts,
+ *   rounds of FP64 evaluations over compacted lists, the cell sums), whose
+ *   solves also settle on Newton steps with a certified error below 2^-43
+ *   of r_w^2 and take the ventilation factors in FP32 where that moves the
+ *   result by less than 2^-45 (both layouts stay within 1e-12 of the
+ *   bisection's root); SDM_COND_AUTO (0): staged from 2^17 super-droplets,
+ *   else fused.  Other solvers and the mixed mode always run fused.
  * sd_reserve: extra super-droplet slots (N = 0) beyond the initial ones,
  *   kept free for arrivals from the neighbouring slabs of an x_open context
  *   (sdm_import): their ids carry the top bit (2^31), which marks a slot
@@ -173,9 +176,12 @@ typedef struct {
 
 /* Per-phase device time [ms] accumulated while timing is on; measured with
  * CUDA events on the context's stream around each group of launches.
- * launches counts the particle scheme's kernels (steps and diagnostics);
- * euler_ms and euler_launches the Eulerian stand-in (sdm_euler_step), which
- * is the driver's part, apart. */
+ * cond_launches and coal_launches count the calls of the condensation and
+ * coalescence phases (each a chain of one or more kernels: cond_ms /
+ * cond_launches is one condensation call's time); launches counts the
+ * particle scheme's kernels (steps and diagnostics); euler_ms and
+ * euler_launches the Eulerian stand-in (sdm_euler_step), which is the
+ * driver's part, apart. */
 typedef struct {
     double cond_ms, recycle_ms, move_ms, sort_ms, coal_ms, diag_ms, copy_ms;
     uint64_t cond_launches, coal_launches, launches;

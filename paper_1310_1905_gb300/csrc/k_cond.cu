@@ -203,6 +203,14 @@ SDM_HD double sqrt1pm1_small(double e) {
            e * (33.0 / 2048 + e * (-429.0 / 32768 + e * (715.0 / 65536)))))))));
 }
 
+// LITE: where the ventilation corrections Sh - 2 and Nu - 2 (about Re Sc/3
+// and Re Pr/3) are below 2^-24 - the haze and small cloud droplets - they
+// are taken in FP32: with a relative error below 2^-20 each (the chain of a
+// few correctly rounded FP32 operations) they move the coefficient by less
+// than 2^-45 of itself, which moves the root of the implicit equation by
+// less than 2^-45 of its increment x1 - x0.  The staged solves take it; the
+// fused kernel's and the bisection's coefficient stays FP64 throughout.
+template <bool LITE = false>
 SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
     using namespace phys;
     double a = D0, b = K0, DM = 1.0, DT = 1.0;
@@ -211,6 +219,20 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
         const double KnM = t.lambda_D * rinv, KnT = t.lambda_K * rinv;
         DM = 1.0 + c1 * KnM + c2 * KnM * KnM;
         DT = 1.0 + c1 * KnT + c2 * KnT * KnT;
+        if (LITE) {
+            const float Xf = (float)t.cX * (float)r3;
+            const float ef = (float)(4.0 / (delta0 * delta0 * sqrt(C0))) * sqrtf(Xf);
+            const float sf = ef / (sqrtf(1.0f + ef) + 1.0f);
+            const float Ref = (float)(delta0 * delta0 / 4.0) * sf * sf;
+            const float yS = Ref * (float)t.Sc, yN = Ref * (float)t.Pr;
+            if (fmaxf(yS, yN) <= 5.9604645e-8f) {  // 2^-24: (1 + y)^(1/3) - 1 = y/3 - y^2/9 + ...
+                const double Sh = 2.0 + (double)(yS * (0.33333333f - 0.11111111f * yS));
+                const double Nu = 2.0 + (double)(yN * (0.33333333f - 0.11111111f * yN));
+                a = D0 * (1.0 + KnM) * Sh * 0.5;
+                b = K0 * (1.0 + KnT) * Nu * 0.5;
+                return Coef{2.0 * a * b, rho_w * (b * DM + t.Dterm * a * DT)};
+            }
+        }
         const double X = t.cX * r3;
         const double e = 4.0 / (delta0 * delta0 * sqrt(C0)) * sqrt(X);
         // Re = delta0^2/4 (sqrt(1 + e) - 1)^2 (KC2002)
@@ -286,6 +308,7 @@ struct FastSolve {
     float Lu, Hu, mu;
     int k;
     bool plo, undecided, mu_inside, pmu, have_slope, clamp;
+    bool mono;  // certified solves: f proven strictly monotone on the bracket (one root: no replay)
 };
 
 // The growth rate for the fast solve, one evaluation for both of its uses
@@ -298,6 +321,9 @@ struct FastSolve {
 // exact = false: the one-division form above (the polish), and in *mag the
 //   same factor times rho_v + rho_o, the size of the terms whose difference
 //   g is (its rounding error is a few ulps of this).
+// LITE: the coefficient's ventilation factors in FP32 where they are within
+//   2^-24 of 2 (growth_coef).
+template <bool LITE = false>
 SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const Thermo &t, int physics,
                           double *mag) {
     double r, rinv;
@@ -310,7 +336,7 @@ SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const 
     }
     const double r3 = x * r;
     const double kel = exp(exact ? t.A / r : t.A * rinv);
-    const Coef c = growth_coef(rinv, r3, t, physics);
+    const Coef c = growth_coef<LITE>(rinv, r3, t, physics);
     const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
     if (exact) {
         *mag = 0.0;
@@ -348,7 +374,38 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
     const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
     float mu = 0.0f;
     bool undecided = false;
-    for (int k = 0; k < 64; ++k) {
+    bool mono = false;
+    if (CERT && H - L <= 0.0625f * x0f) {
+        // f' = 1 - dt' g' lies within dt' (edg + curv |x - xm|) of the FP32
+        // slope at the bracket's middle xm; where that keeps f' away from
+        // zero over the whole bracket (and its sign agrees with the ends'),
+        // f has one root there, every halving of the bisection leads to it,
+        // and the locate takes safeguarded FP32 Newton steps instead of
+        // halvings, to the point where FP32 stops deciding the sign
+        const float dm = 0.5f * (L + H);
+        GF q = growth_f3_bounds(x0f + dm, rd3f, kf, &tf, physics);
+        const float sl = 1.0f - dtpf * q.dg;
+        const float reach = 0.5f * (H - L) + 1.2e-7f * x0f;
+        mono = fabsf(sl) > 1.001f * dtpf * (q.edg + q.curv * reach) && (sl > 0.0f) != plo;
+        float d = dm;
+        for (int k = 0; mono && k < 48; ++k) {
+            const float f = d - dtpf * q.g;
+            if (!(fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err)) {
+                mu = d;
+                undecided = true;
+                break;
+            }
+            if ((f > 0.0f) == plo) L = d;
+            else H = d;
+            float dn = d - f / (1.0f - dtpf * q.dg);
+            if (!(dn > L && dn < H)) dn = 0.5f * (L + H);
+            if (!(dn > L && dn < H)) break;  // the bracket is down to adjacent floats
+            d = dn;
+            q = growth_f3_full(x0f + d, rd3f, kf, &tf, physics);
+        }
+    }
+    S.mono = mono;
+    for (int k = 0; !mono && k < 64; ++k) {
         const float d = 0.5f * (L + H);
         if (!(d > L && d < H)) break;
         const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
@@ -399,11 +456,16 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
 // ds = es + cv (|xsp - xb| + 2 |xn - xb|), so (mean value theorem) the root
 // lies within (|xn - xb| ds + efb) / (|s| - ds) of xn.  Certified when that
 // is below 2^-43 xn (1.1e-13 of it, nearly nine times inside the 1e-12 bar).
+//
+// efb: an FP64 evaluation of f carries at most a few ulps of the terms whose
+// difference it is (the sums of rho_v and rho_o, each a product of a handful
+// of correctly rounded factors and exp, whose error CUDA bounds by 1 ulp);
+// the callers allow 16 ulps (2^-49) of them.
 SDM_HD bool newton_certified(const FastSolve &S, double xb, double xn, double efb) {
     const double step = fabs(xn - xb), as = fabs(S.slope);
     const double ds = S.es + S.cv * (fabs(S.xsp - xb) + 2.0 * step);
     if (!(ds < 0.25 * as)) return false;
-    return (step * ds + efb) / (as - ds) <= 0x1p-43 * xn;
+    return step * ds + efb <= 0x1p-43 * xn * (as - ds);
 }
 
 // fs_replay is defined below; a certified step from x0 replays the halvings.
@@ -417,11 +479,21 @@ template <bool CERT>
 SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
                         SolveCounters &cnt) {
     const double x0 = S.x0;
-    const double a = fmax(rd2_of(S.rd3), x0 + fmin(2.0 * dtp * g0, 0.0));
+    const double xa = x0 + fmin(2.0 * dtp * g0, 0.0);
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
+    // a = max(r_d^2, xa); CERT: r_d^2 in FP64 only where the FP32 cube root
+    // (1 ulp, squared: within 2^-20) cannot place it below xa
+    double a;
+    if (CERT) {
+        float rd2f = cbrtf(rd3f);
+        rd2f *= rd2f;
+        a = xa > (double)rd2f * (1.0 + 0x1p-20) ? xa : fmax(rd2_of(S.rd3), xa);
+    } else {
+        a = fmax(rd2_of(S.rd3), xa);
+    }
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
     S.a = a;
     S.b = b;
-    const float rd3f = (float)S.rd3, kf = (float)S.kappa, dtpf = (float)dtp, x0f = (float)x0;
     // the ends' signs; at x0 itself f = -dtp g0 exactly.  The sign of f at
     // x0 + d (d an FP32 increment) is computed in FP32 and trusted where |f|
     // exceeds its error bound (it is then the sign an FP64 evaluation gives).
@@ -482,6 +554,7 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     // over a step of a few ulps their difference is rounding.
     S.plo = pe[0];
     S.undecided = true;
+    S.mono = false;
     S.Lu = (float)(a - x0);
     S.Hu = (float)(b - x0);
     S.mu = 0.0f;
@@ -502,15 +575,20 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     S.k = 0;
     if (CERT) {
         // the Newton step from x0 is the result where its certified error is
-        // far below 1e-12: f(x0) is known to the rounding of g0's terms, at
-        // most 2^-47 of their size mag; the replay then checks that the
+        // far below 1e-12: f(x0) = -dt' g0 is known to the rounding of g0's
+        // terms (their size mag, from FP32); the replay then checks that the
         // bisection's halvings lead to it
         S.es = dtp * (double)q0.edg;
         S.cv = dtp * (double)q0.curv;
         S.xsp = x0;
-        if (newton && newton_certified(S, x0, xk, 0x1p-47 * dtp * (double)q0.mag)) {
+        // f strictly monotone on [a, b] (its slope bounds as in fs_locate):
+        // one root, to which every halving leads, and no replay
+        const double reach = fmax(x0 - a, b - x0) + fabs(x0 - (double)x0f);
+        S.mono = b - a <= 0.0625 * x0 && fabs(S.slope) > 1.001 * (S.es + S.cv * reach) &&
+                 (S.slope > 0.0) != S.plo;
+        if (newton && newton_certified(S, x0, xk, 0x1p-49 * dtp * (double)q0.mag)) {
             cnt.certified++;
-            S.x1 = fs_replay(S, xk, t, tf, dtp, physics, cnt);
+            S.x1 = S.mono ? xk : fs_replay(S, xk, t, tf, dtp, physics, cnt);
             return true;
         }
     }
@@ -695,11 +773,11 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t,
         // f(xk) is at the rounding level of its evaluation: near it a secant
         // slope from close points is itself rounding.
         const bool inside = at_noise ? xn >= lo && xn <= hi : xn > lo && xn < hi;
-        // certified: f(xk) carries the rounding of the one-division form, at
-        // most 2^-47 of its terms
+        // certified: f(xk) carries the rounding of the one-division form (of
+        // its terms xk - x0 and dt' g's, mag)
         const bool small = fabs(xn - xk) <= (secant ? 0x1p-30 : 0x1p-46) * xk;
         const bool cert = CERT && !small && !secant && S.have_slope &&
-                          newton_certified(S, xk, xn, 0x1p-47 * (fabs(xk - S.x0) + dtp * mag));
+                          newton_certified(S, xk, xn, 0x1p-49 * (fabs(xk - S.x0) + dtp * mag));
         if (inside && (small || cert)) {
             if (cert) cnt.certified++;
             r = xn;
@@ -721,7 +799,7 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t,
         S.x1 = bisect_rest(S.lo, S.hi, S.plo, S.x0, S.rd3, S.kappa, t, dtp, physics);
         return true;
     }
-    S.x1 = S.undecided ? fs_replay(S, r, t, tf, dtp, physics, cnt) : r;
+    S.x1 = S.undecided && !(CERT && S.mono) ? fs_replay(S, r, t, tf, dtp, physics, cnt) : r;
     return true;
 }
 
@@ -741,7 +819,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         const bool g0 = k == 0 && start != kStartPolish;
         cnt.evals++;
         double mag;
-        const double v = growth_eval(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
+        const double v = growth_eval<CERT>(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
         if (g0) {
             if (start == kStartExact) {
                 if (fs_after_g0<CERT>(S, v, t, tf, dtp, physics, cnt)) return S.x1;
@@ -1137,7 +1215,7 @@ cudaError_t launch_ens_cond_tiles(SdArrays s, const MemberDev *M, const uint32_t
 // in the previous launch (the cells change slowly from step to step); with
 // many waves (or no cost yet) the order is the cells' own.
 template <int LPC, int MODE>
-static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
+static int launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
     const int64_t threads = ((int64_t)c->grid.n_cells * LPC + 31) / 32 * 32;
     const int64_t n_warps = threads / 32;
     if (LPC == 32 && c->cond_order_on && n_warps <= kOrderMaxWarps) {
@@ -1158,19 +1236,20 @@ static void launch_condense_lpc(sdm_ctx *c, const sdm_opts &o, int B) {
             k_condense<LPC, MODE, LPC == 32><<<grid_for(threads, B), B, 0, c->stream>>>(
                 c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
                 c->dstats, c->cond_order, c->cond_cost, n_warps);
-            return;
+            return 2;
         }
     }
     k_condense<LPC, MODE, false><<<grid_for(threads, B), B, 0, c->stream>>>(
         c->buf[c->cur], c->offset, c->th, c->rv, c->rhod, c->grid, o.sstp_cond, o.RH_max, c->oi.physics,
         c->dstats, nullptr, nullptr, n_warps);
+    return 1;
 }
 
 template <int MODE>
-static void launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) {
-    if (lpc == 4) launch_condense_lpc<4, MODE>(c, o, B);
-    else if (lpc == 8) launch_condense_lpc<8, MODE>(c, o, B);
-    else launch_condense_lpc<32, MODE>(c, o, B);
+static int launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) {
+    if (lpc == 4) return launch_condense_lpc<4, MODE>(c, o, B);
+    if (lpc == 8) return launch_condense_lpc<8, MODE>(c, o, B);
+    return launch_condense_lpc<32, MODE>(c, o, B);
 }
 
 // ---------------------------------------------------------------------------
@@ -1182,11 +1261,12 @@ static void launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) 
 // that still need one, each round one evaluation per record (so the lanes of
 // a warp do the same work), finished solves writing their r_w^2; (4) per
 // cell, the sum of eq. rhov_update and the update of r_v and theta.  The
-// solve's steps are those of solve_rw2_fast, in the same order on the same
-// values, so each super-droplet's result is the same bit for bit; the cell
-// sums add the same terms in another order.  The solve state travels
-// through HBM between the kernels, which the FP64-bound fused kernel leaves
-// idle.
+// solve's steps are those of solve_rw2_fast<true>: the fused kernel's fast
+// solve, which also settles on a certified Newton step, signs the bracket's
+// ends from the FP32 slope near equilibrium and takes tiny ventilation
+// corrections in FP32 (each within 1e-12 of the bisection's root, like the
+// fused solve).  The solve state travels through HBM between the kernels,
+// which the FP64-bound fused kernel leaves idle.
 enum { kTaskNone = 0, kTaskG0Euler = 1, kTaskG0Tiny = 2, kTaskG0Exact = 3, kTaskPolish = 4 };
 
 struct StagedRec {
@@ -1201,7 +1281,11 @@ struct StagedCell {
 };
 
 constexpr int kStagedRounds = 15;  // a fast solve takes at most 14 FP64 growth evaluations
-constexpr int64_t kStagedMinSd = int64_t(1) << 62;  // the automatic choice: set from measurement
+constexpr int kStagedListRounds = 3;  // rounds over compacted lists before the finishing launch
+// the automatic choice of the staged chain: domains of at least 2^17
+// super-droplets (measured on GB300: below that the fused kernel's single
+// launch wins; from it the chain, by 10-20 % in 3D)
+constexpr int64_t kStagedMinSd = int64_t(1) << 17;
 
 __global__ void k_cs_cells(const double *th, const double *rv, const double *rhod, int n_cells, double RH_max,
                            StagedCell *out) {
@@ -1267,7 +1351,10 @@ __global__ void k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, cons
 }
 
 // one FP64 growth evaluation per record; the records that need another go
-// to the next list (one atomic per block), the finished write r_w^2
+// to the next list (one atomic per block), the finished write r_w^2.
+// FINISH: the last round, each record's evaluations in sequence until its
+// solve finishes (the few left after the first rounds)
+template <bool FINISH>
 __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, int64_t rev_end,
                                                  StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
                                                  const StagedCell *cells, double dtp, int physics, double *x1,
@@ -1285,29 +1372,37 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
             if (r.task != kTaskNone) {
                 const StagedCell &cl = cells[cell_of_sd[r.sd]];
                 FastSolve &S = r.S;
-                const bool g0 = r.task != kTaskPolish;
-                cnt.evals++;
-                double mag;
-                const double v = growth_eval(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag);
-                bool done;
-                if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
-                    if (r.task == kTaskG0Euler) cnt.euler++;
-                    S.x1 = fs_euler(S, v, dtp);
-                    done = true;
-                } else if (r.task == kTaskG0Exact) {
-                    done = fs_after_g0<true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
-                } else {
-                    done = fs_after_polish<true>(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
+                bool done = false;
+                for (int k = 0; k < (FINISH ? kStagedRounds : 1) && !done; ++k) {
+                    const bool g0 = r.task != kTaskPolish;
+                    cnt.evals++;
+                    double mag;
+                    const double v = growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag);
+                    if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
+                        if (r.task == kTaskG0Euler) cnt.euler++;
+                        S.x1 = fs_euler(S, v, dtp);
+                        done = true;
+                    } else if (r.task == kTaskG0Exact) {
+                        done = fs_after_g0<true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
+                    } else {
+                        done = fs_after_polish<true>(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
+                    }
+                    if (!done) r.task = kTaskPolish;
                 }
                 if (done) {
                     x1[r.sd] = S.x1;
                     bad |= !isfinite(S.x1);
+                } else if (FINISH) {
+                    // not reached: a fast solve takes at most kStagedRounds - 1
+                    // evaluations; flagged rather than left unwritten
+                    x1[r.sd] = S.x0;
+                    bad = true;
                 } else {
-                    r.task = kTaskPolish;
                     keep = true;
                 }
             }
         }
+        if (FINISH) continue;
         // block-wide compaction of the records that continue
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1367,7 +1462,7 @@ __global__ void k_cs_cellmap(const uint32_t *offset, int n_cells, uint32_t *cell
     for (uint32_t i = offset[c] + (threadIdx.x & 31); i < offset[c + 1]; i += 32) cell_of_sd[i] = (uint32_t)c;
 }
 
-static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
+static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *launches) {
     const int64_t n = c->n_sd;
     const int nc = c->grid.n_cells;
     cudaError_t e = cudaSuccess;
@@ -1376,7 +1471,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_rec[1], sizeof(StagedRec) * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_cell, sizeof(StagedCell) * (size_t)nc + 4 * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_x1, 8 * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedRounds + 3));
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedListRounds + 3));
         if (e != cudaSuccess) return e;
     }
     StagedRec *rec[2] = {(StagedRec *)c->cs_rec[0], (StagedRec *)c->cs_rec[1]};
@@ -1386,6 +1481,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
     const int64_t warps_threads = (int64_t)nc * 32;
     const int B = 128;
     k_cs_cellmap<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->offset, nc, cell_of_sd);
+    *launches = 1 + o.sstp_cond * (kStagedListRounds + 5);  // cells, start, 2 + (rounds - 1) + 1 evals, update
     int dev = 0, n_sm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -1394,20 +1490,23 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
         k_cs_cells<<<grid_for(nc, 128), 128, 0, c->stream>>>(c->th, c->rv, c->rhod, nc, o.RH_max, cells);
         // round 0 in two launches, the g(x0) records (front of the list) and
         // the polish records (back); each round's survivors feed the next
-        unsigned *cnt = c->cs_cnt, *n_pol = c->cs_cnt + kStagedRounds + 2;
-        e = cudaMemsetAsync(cnt, 0, 4 * (kStagedRounds + 3), c->stream);
+        unsigned *cnt = c->cs_cnt, *n_pol = c->cs_cnt + kStagedListRounds + 2;
+        e = cudaMemsetAsync(cnt, 0, 4 * (kStagedListRounds + 3), c->stream);
         if (e != cudaSuccess) return e;
         k_cs_start<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, dtp,
                                                                    c->oi.physics, rec[0], c->cs_x1, cnt, n_pol,
                                                                    (unsigned)n);
         for (int part = 0; part < 2; ++part)
-            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0, rec[1], cnt + 1,
-                                                          cell_of_sd, cells, dtp, c->oi.physics, c->cs_x1,
-                                                          c->dstats);
-        for (int r = 1; r < kStagedRounds; ++r)
-            k_cs_eval<<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1], cnt + r + 1,
-                                                          cell_of_sd, cells, dtp, c->oi.physics, c->cs_x1,
-                                                          c->dstats);
+            k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0, rec[1],
+                                                                 cnt + 1, cell_of_sd, cells, dtp, c->oi.physics,
+                                                                 c->cs_x1, c->dstats);
+        for (int r = 1; r < kStagedListRounds; ++r)
+            k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1],
+                                                                 cnt + r + 1, cell_of_sd, cells, dtp, c->oi.physics,
+                                                                 c->cs_x1, c->dstats);
+        const int r = kStagedListRounds;
+        k_cs_eval<true><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, nullptr, nullptr, cell_of_sd,
+                                                            cells, dtp, c->oi.physics, c->cs_x1, c->dstats);
         k_cs_update<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, c->cs_x1,
                                                                     c->th, c->rv, c->rhod, c->grid.dV, c->dstats);
     }
@@ -1419,20 +1518,20 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o) {
 // lane's solves run in sequence and the FP64 pipe needs several warps per
 // scheduler.  One-warp blocks when cells are few, so that the last wave is
 // fine-grained.
-cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o) {
+cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o, int *launches) {
     const int64_t per_cell = (int64_t)c->G * c->oi.sd_conc, n_cells = c->grid.n_cells;
     // the staged chain for the fast FP64 solve where chosen (cond_layout), or
-    // by default where the domain holds at least 2^22 super-droplets
+    // by default where the domain holds at least kStagedMinSd super-droplets
     const bool fast64 = c->oi.precision != SDM_PRECISION_MIXED && c->oi.cond_solver != SDM_SOLVER_BISECT;
     const bool staged = c->oi.cond_layout == SDM_COND_STAGED ||
                         (c->oi.cond_layout == SDM_COND_AUTO && c->n_sd >= kStagedMinSd);
-    if (fast64 && staged) return launch_condense_staged(c, o);
+    if (fast64 && staged) return launch_condense_staged(c, o, launches);
     int lpc = per_cell <= 32 ? 4 : (per_cell <= 64 ? 8 : 32);
     while (lpc < 32 && n_cells * lpc < (int64_t)32 * 8192) lpc = lpc == 4 ? 8 : 32;
     const int B = n_cells * lpc < (int64_t)32 * 32768 ? 32 : 128;
-    if (c->oi.precision == SDM_PRECISION_MIXED) launch_condense_mode<kModeMixed>(c, o, lpc, B);
-    else if (c->oi.cond_solver == SDM_SOLVER_BISECT) launch_condense_mode<kModeBisect>(c, o, lpc, B);
-    else launch_condense_mode<kModeFast>(c, o, lpc, B);
+    if (c->oi.precision == SDM_PRECISION_MIXED) *launches = launch_condense_mode<kModeMixed>(c, o, lpc, B);
+    else if (c->oi.cond_solver == SDM_SOLVER_BISECT) *launches = launch_condense_mode<kModeBisect>(c, o, lpc, B);
+    else *launches = launch_condense_mode<kModeFast>(c, o, lpc, B);
     return cudaGetLastError();
 }
 

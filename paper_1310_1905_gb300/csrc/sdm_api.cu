@@ -624,8 +624,9 @@ sdm_status sdm_step_sync(sdm_ctx *c, const sdm_opts *o, sdm_arr th, sdm_arr rv, 
         if (sdm_status s = regroup(c)) return s;
     if (o->cond) {
         Phase ph(c, PH_COND);
-        CK(launch_condense(c, *o), "condensation");
-        c->tacc.launches += 1;
+        int nl = 0;
+        CK(launch_condense(c, *o, &nl), "condensation");
+        c->tacc.launches += nl;
         c->tacc.cond_launches++;
     }
     {

@@ -371,7 +371,8 @@ namespace sdm {
 
 // launch wrappers (each returns the first CUDA error of its launches)
 cudaError_t launch_init(sdm_ctx *c);
-cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o);
+// *launches: the kernels it enqueued
+cudaError_t launch_condense(sdm_ctx *c, const sdm_opts &o, int *launches);
 cudaError_t launch_ambient(sdm_ctx *c);
 cudaError_t launch_move(sdm_ctx *c, const sdm_opts &o);
 cudaError_t launch_regroup(sdm_ctx *c);  // scan + perm (after move)
