@@ -61,22 +61,42 @@ COND_ALGO_FLOPS_PER_SD_SUBSTEP = 450.0
 # (68 B); the regrouping reads the cell and moves the state (116 B in 2D,
 # 132 B in 3D)
 HBM_BYTES_PER_SD_STEP = {"icmw_2d": 40 + 68 + 116, "updraft_3d": 40 + 68 + 132, "golovin_box": 68 + 116}
-# ncu on k_condense: the FP64 flops it executes (2 DFMA + DADD + DMUL) per
-# SD-substep, its DRAM bytes read + written per launch per super-droplet and
-# the share of active cycles its FP64 pipe is busy, with the capture they
-# come from.  Mixed precision too is bound by its FP64 part (the solves near
+# ncu on the condensation call: the FP64 flops it executes (2 DFMA + DADD +
+# DMUL) per SD-substep, its DRAM bytes read + written per call per
+# super-droplet and the share of its cycles the FP64 pipe is busy, with the
+# capture they come from, by workload, precision and layout.  "fused": one
+# k_condense launch; "staged": the chain of k_cs_* launches of one call (10
+# substeps), whose solve records travel through HBM between the launches.
+# Mixed precision too is bound by its FP64 part (the solves near
 # activation): its FP32 work is about 1 % of the FP32 peak.
 COND_FP64 = {
-    ("icmw_2d", "fp64"): dict(flops_per_sd_substep=649.85, dram_bytes_per_sd=11.835e6 / 360000,
-                              fp64_pipe_active=0.7175, capture="2D case, 360 000 SDs, one launch"),
-    ("icmw_2d", "mixed"): dict(flops_per_sd_substep=178.07, dram_bytes_per_sd=11.895e6 / 360000,
-                               fp64_pipe_active=0.5272, capture="2D case, 360 000 SDs, one launch"),
-    ("updraft_3d", "fp64"): dict(flops_per_sd_substep=667.07, dram_bytes_per_sd=331.62e6 / 8388608,
-                                 fp64_pipe_active=0.7364,
-                                 capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic scaled by the "
-                                         "SDs of a launch (it grows in proportion: 39.5 B per SD against 40 B "
-                                         "algorithmic)"),
+    ("icmw_2d", "fp64", "fused"): dict(kernel="k_condense", flops_per_sd_substep=649.85,
+                                       dram_bytes_per_sd=11.835e6 / 360000, fp64_pipe_active=0.7175,
+                                       capture="2D case, 360 000 SDs, one launch"),
+    ("icmw_2d", "mixed", "fused"): dict(kernel="k_condense", flops_per_sd_substep=178.07,
+                                        dram_bytes_per_sd=11.895e6 / 360000, fp64_pipe_active=0.5272,
+                                        capture="2D case, 360 000 SDs, one launch"),
+    ("updraft_3d", "fp64", "fused"): dict(kernel="k_condense", flops_per_sd_substep=667.07,
+                                          dram_bytes_per_sd=331.62e6 / 8388608, fp64_pipe_active=0.7364,
+                                          capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic "
+                                                  "scaled by the SDs of a launch"),
+    ("icmw_2d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=329.65,
+                                        dram_bytes_per_sd=4552.1, fp64_pipe_active=0.452,
+                                        capture="2D case, 360 000 SDs, one call (81 launches)"),
+    ("updraft_3d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=320.67,
+                                           dram_bytes_per_sd=6188.7, fp64_pipe_active=0.654,
+                                           capture="3D updraft, 32x32x128 columns (4.2 M SDs), one call (81 "
+                                                   "launches); traffic scaled by the SDs of a call"),
 }
+# the library's own choice of layout (cond_layout = auto): the staged chain
+# for the FP64 fast solve from 2^17 super-droplets
+STAGED_MIN_SD = 1 << 17
+
+
+def cond_layout_of(args, n_sd: int) -> str:
+    if args.precision != "fp64" or args.cond_layout == "fused":
+        return "fused"
+    return "staged" if args.cond_layout == "staged" or n_sd >= STAGED_MIN_SD else "fused"
 
 
 def parse():
@@ -94,6 +114,9 @@ def parse():
     ap.add_argument("--nz", type=int, default=None,
                     help="updraft_3d: levels, when they differ from --cells (a profile of fewer columns of the "
                          "full-height domain)")
+    ap.add_argument("--probe-seconds", type=float, default=2.0,
+                    help="length of the sustained FP64 throughput probe before the workload (shorter for profiling "
+                         "runs, whose launch lists would otherwise hold its launches)")
     ap.add_argument("--cond-layout", default="auto", choices=["auto", "fused", "staged"],
                     help="condensation kernels: fused, staged, or chosen by domain size")
     ap.add_argument("--profile-one-step", action="store_true",
@@ -199,7 +222,7 @@ def run_gpu(args, rank: int, world: int):
     rhod = torch.tensor(w.rhod, dtype=torch.float64, device="cuda")
     Cs = [None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
           for a in (w.rhoCx, w.rhoCy, w.rhoCz)]
-    device = sdm.sdm_probe_device(2.0)  # SM count and FP64 throughput, before the workload
+    device = sdm.sdm_probe_device(args.probe_seconds)  # SM count and FP64 throughput, before the workload
     p = sdm.Particles(w.cfg, th, rv, rhod, *Cs, stream=stream.cuda_stream, precision=args.precision)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -652,11 +675,12 @@ def main():
     value = whole_job_value(res["n_sd"], args.steps, world, res["t_dev"])
     tim = res["timing"]
     pk = peaks()
-    # dominant kernel: condensation, bound by FP64 arithmetic.  achieved =
-    # the algorithmic FP64 flops of the solve per SD-substep x the
-    # SD-substeps of one launch / the launch's CUDA-event time; peak = the
-    # FP64 FMA throughput measured on this device (sustained: one launch
-    # runs for most of a step)
+    # dominant kernel: condensation, bound by FP64 arithmetic, one call of
+    # it (one k_condense launch, or the staged chain of k_cs_* launches)
+    # timed with CUDA events on the context's stream.  achieved = the
+    # algorithmic FP64 flops of the solve per SD-substep x the SD-substeps
+    # of one call / the call's time; peak = the FP64 FMA throughput
+    # measured on this device (sustained: one call runs for most of a step)
     cond_ms = tim["cond_ms"] / max(1, tim["cond_launches"])
     clk = res["clocks"]
     dev = res["device"]
@@ -666,26 +690,25 @@ def main():
     units = res["n_sd"] * w.opts["sstp_cond"]
     hbm = pk.get("hbm_gbs", 6800.0)
     hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "of fallback 6800 GB/s"
-    if (args.workload, args.precision) in COND_FP64:
-        k = COND_FP64[(args.workload, args.precision)]
+    layout = cond_layout_of(args, res["n_sd"])
+    if tim["cond_launches"] > 0:
+        k = COND_FP64.get((args.workload, args.precision, layout))
         achieved = COND_ALGO_FLOPS_PER_SD_SUBSTEP * units / (cond_ms * 1e-3) / 1e12
-        executed = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
-        roof = dict(kernel="k_condense", bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
-                    frac=achieved / fp64_peak, traffic=k["dram_bytes_per_sd"] * res["n_sd"],
+        roof = dict(kernel=k["kernel"] if k else ("condensation chain (k_cs_*)" if layout == "staged"
+                                                  else "k_condense"),
+                    layout=layout, bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
+                    frac=achieved / fp64_peak, traffic=k["dram_bytes_per_sd"] * res["n_sd"] if k else None,
                     algorithmic_flops_per_sd_substep=COND_ALGO_FLOPS_PER_SD_SUBSTEP,
                     launch_ms=cond_ms, sd_substeps_per_launch=units,
                     peak_source="of measured: FP64 FMA chains on this device (sdm_probe_device), sustained "
                                 f"{dev['fp64_tflops_sustained']:.3f}, burst {dev['fp64_tflops_burst']:.3f} TFLOP/s",
                     derived_peak=dict(value=fp64_derived, how=f"4 FP64 flop/SM/clk x {dev['n_sm']} SMs (device "
-                                                              f"query) x {sm_mhz:.0f} MHz (sampled)"),
-                    executed=dict(flops_per_sd_substep=k["flops_per_sd_substep"], achieved=executed,
-                                  frac=executed / fp64_peak, fp64_pipe_active=k["fp64_pipe_active"],
-                                  counters=k["capture"]))
-    elif tim["cond_launches"] > 0:
-        bytes_per_launch = 40.0 * res["n_sd"]
-        achieved = bytes_per_launch / (cond_ms * 1e-3) / 1e9
-        roof = dict(kernel="k_condense", bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
-                    frac=achieved / hbm, traffic=None, peak_source=hbm_src)
+                                                              f"query) x {sm_mhz:.0f} MHz (sampled)"))
+        if k:
+            executed = k["flops_per_sd_substep"] * units / (cond_ms * 1e-3) / 1e12
+            roof["executed"] = dict(flops_per_sd_substep=k["flops_per_sd_substep"], achieved=executed,
+                                    frac=executed / fp64_peak, fp64_pipe_active=k["fp64_pipe_active"],
+                                    counters=k["capture"])
     else:  # no condensation (the Golovin box): coalescence, 68 B per SD-step (read 36, write 32)
         coal_ms = tim["coal_ms"] / max(1, tim["coal_launches"])
         achieved = 68.0 * res["n_sd"] / (coal_ms * 1e-3) / 1e9

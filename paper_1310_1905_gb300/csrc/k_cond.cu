@@ -321,13 +321,16 @@ struct FastSolve {
 // exact = false: the one-division form above (the polish), and in *mag the
 //   same factor times rho_v + rho_o, the size of the terms whose difference
 //   g is (its rounding error is a few ulps of this).
-// LITE: the coefficient's ventilation factors in FP32 where they are within
-//   2^-24 of 2 (growth_coef).
+// LITE (the staged solves): the coefficient's ventilation factors in FP32
+//   where they are within 2^-24 of 2 (growth_coef); r and A/r from the
+//   reciprocal square root in both forms; the Kelvin factor e^(A/r) by its
+//   Taylor series where A/r <= 1/32.  Each changes g by a few ulps of its
+//   terms, the rounding level the certified steps already allow for.
 template <bool LITE = false>
 SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const Thermo &t, int physics,
                           double *mag) {
     double r, rinv;
-    if (exact) {
+    if (exact && !LITE) {
         r = sqrt(x);
         rinv = 1.0 / r;
     } else {
@@ -335,7 +338,16 @@ SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const 
         r = x * rinv;
     }
     const double r3 = x * r;
-    const double kel = exp(exact ? t.A / r : t.A * rinv);
+    const double y = exact && !LITE ? t.A / r : t.A * rinv;
+    double kel;
+    if (LITE && y <= 0.03125) {
+        // e^y by its Taylor series to y^8: the remainder is below
+        // y^9/9! e^y < 2e-19 for y <= 1/32 (droplets above about 40 nm)
+        kel = 1.0 + y * (1.0 + y * (1.0 / 2 + y * (1.0 / 6 + y * (1.0 / 24 + y * (1.0 / 120 + y * (1.0 / 720 +
+              y * (1.0 / 5040 + y * (1.0 / 40320))))))));
+    } else {
+        kel = exp(y);
+    }
     const Coef c = growth_coef<LITE>(rinv, r3, t, physics);
     const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
     if (exact) {
@@ -461,9 +473,17 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
 // difference it is (the sums of rho_v and rho_o, each a product of a handful
 // of correctly rounded factors and exp, whose error CUDA bounds by 1 ulp);
 // the callers allow 16 ulps (2^-49) of them.
+// 1/s for the certified Newton steps without an FP64 division: the FP32
+// reciprocal (within 2^-23 of 1/s) and one Newton iteration, within 2^-45;
+// newton_certified counts that as a slope error of 2^-44 |s|.
+SDM_HD double rcp_slope(double s) {
+    const double r0 = (double)(1.0f / (float)s);
+    return r0 * fma(-s, r0, 2.0);
+}
+
 SDM_HD bool newton_certified(const FastSolve &S, double xb, double xn, double efb) {
     const double step = fabs(xn - xb), as = fabs(S.slope);
-    const double ds = S.es + S.cv * (fabs(S.xsp - xb) + 2.0 * step);
+    const double ds = S.es + S.cv * (fabs(S.xsp - xb) + 2.0 * step) + 0x1p-44 * as;
     if (!(ds < 0.25 * as)) return false;
     return step * ds + efb <= 0x1p-43 * xn * (as - ds);
 }
@@ -567,7 +587,7 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     S.have_slope = true;
     S.sdx = S.sdf = 1.0;
     const double f0 = -dtp * g0;
-    double xk = S.slope > 0.0 ? x0 - f0 / S.slope : 0.5 * (a + b);
+    double xk = S.slope > 0.0 ? x0 - f0 * (CERT ? rcp_slope(S.slope) : 1.0 / S.slope) : 0.5 * (a + b);
     const bool newton = xk > a && xk < b;
     if (!newton) xk = 0.5 * (a + b);
     S.xp = S.fp = 0.0;
@@ -763,7 +783,7 @@ SDM_HD bool fs_after_polish(FastSolve &S, double v, double mag, const Thermo &t,
             xn = xk - fk * (S.sdx / S.sdf);
             S.have_slope = false;
         } else {
-            xn = S.slope != 0.0 ? xk - fk / S.slope : 0.5 * (lo + hi);
+            xn = S.slope != 0.0 ? xk - fk * (CERT ? rcp_slope(S.slope) : 1.0 / S.slope) : 0.5 * (lo + hi);
         }
         // the secant converges superlinearly: once its step is below 2^-30 x
         // the error left is of order (2^-30)(previous step) x, far below
