@@ -1374,17 +1374,64 @@ __global__ void k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, cons
 // to the next list (one atomic per block), the finished write r_w^2.
 // FINISH: the last round, each record's evaluations in sequence until its
 // solve finishes (the few left after the first rounds)
+// Which branches of growth_eval<true> an evaluation at x takes (FP32
+// estimate): 0 the Kelvin factor by exp (A/r > 1/32) and the ventilation
+// corrections in FP32 (LITE), 1 the same with the Kelvin factor's series,
+// 2 the corrections' binomial series, 3 the cube roots, 4 the cube roots and
+// Re^0.077 (Re > 1).
+SDM_HD int vent_class(float x, const ThermoF &tf, int physics) {
+    using namespace phys;
+    const float r = sqrtf(x);
+    const int kel = tf.A > 0.03125f * r ? 0 : 1;
+    if (!physics) return kel;
+    const float r3 = x * r;
+    const float e = (float)(4.0 / (delta0 * delta0 * sqrt(C0))) * sqrtf(tf.cX * r3);
+    const float sq = e / (sqrtf(1.0f + e) + 1.0f);
+    const float Re = (float)(delta0 * delta0 / 4.0) * sq * sq, y = Re * fmaxf(tf.Sc, tf.Pr);
+    return y <= 5.9604645e-8f ? kel : y <= 0.015625f ? 2 : Re <= 1.0f ? 3 : 4;
+}
+
 template <bool FINISH>
 __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, int64_t rev_end,
                                                  StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
                                                  const StagedCell *cells, double dtp, int physics, double *x1,
                                                  DevStats *st) {
-    __shared__ unsigned s_warp[8], s_base;
+    constexpr int kKeys = 16;  // 3 kinds of record x 5 classes of evaluation, then the empty slots
+    __shared__ unsigned s_warp[8], s_base, s_cnt[kKeys];
+    __shared__ uint16_t s_perm[256];
     const unsigned n = *n_in;
     SolveCounters cnt{0, 0, 0, 0};
     bool bad = false;
     for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const unsigned t = base + threadIdx.x;
+        // the tile's records regrouped by the branches their evaluation
+        // takes (the task, then growth_coef's), so that the lanes of a warp
+        // run the same code; each record's arithmetic is unchanged
+        unsigned t = base + threadIdx.x;
+        int key = kKeys - 1;
+        if (t < n) {
+            const StagedRec &q = rev_end ? in[rev_end - 1 - t] : in[t];
+            if (q.task != kTaskNone) {
+                const bool g0 = q.task != kTaskPolish;
+                const int kind = !g0 ? 0 : q.task == kTaskG0Exact ? 1 : 2;
+                key = 5 * kind + vent_class((float)(g0 ? q.S.x0 : q.S.xk), cells[cell_of_sd[q.sd]].tf, physics);
+            }
+        }
+        if (threadIdx.x < kKeys) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned rank = atomicAdd(&s_cnt[key], 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int q = 0; q < kKeys; ++q) {
+                const unsigned v = s_cnt[q];
+                s_cnt[q] = tot;
+                tot += v;
+            }
+        }
+        __syncthreads();
+        s_perm[s_cnt[key] + rank] = (uint16_t)threadIdx.x;
+        __syncthreads();
+        t = base + s_perm[threadIdx.x];
         bool keep = false;
         StagedRec r;
         if (t < n) {
