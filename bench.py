@@ -81,10 +81,10 @@ COND_FP64 = {
                                           capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic "
                                                   "scaled by the SDs of a launch"),
     ("icmw_2d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=329.65,
-                                        dram_bytes_per_sd=4552.1, fp64_pipe_active=0.452,
+                                        dram_bytes_per_sd=4537.1, fp64_pipe_active=0.418,
                                         capture="2D case, 360 000 SDs, one call (81 launches)"),
     ("updraft_3d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=320.67,
-                                           dram_bytes_per_sd=6188.7, fp64_pipe_active=0.654,
+                                           dram_bytes_per_sd=6188.1, fp64_pipe_active=0.621,
                                            capture="3D updraft, 32x32x128 columns (4.2 M SDs), one call (81 "
                                                    "launches); traffic scaled by the SDs of a call"),
 }

@@ -387,6 +387,7 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
     float mu = 0.0f;
     bool undecided = false;
     bool mono = false;
+    GF q;  // CERT, mono: the FP32 growth rate and its bounds at the last Newton point
     if (CERT && H - L <= 0.0625f * x0f) {
         // f' = 1 - dt' g' lies within dt' (edg + curv |x - xm|) of the FP32
         // slope at the bracket's middle xm; where that keeps f' away from
@@ -395,7 +396,7 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
         // and the locate takes safeguarded FP32 Newton steps instead of
         // halvings, to the point where FP32 stops deciding the sign
         const float dm = 0.5f * (L + H);
-        GF q = growth_f3_bounds(x0f + dm, rd3f, kf, &tf, physics);
+        q = growth_f3_bounds(x0f + dm, rd3f, kf, &tf, physics);
         const float sl = 1.0f - dtpf * q.dg;
         const float reach = 0.5f * (H - L) + 1.2e-7f * x0f;
         mono = fabsf(sl) > 1.001f * dtpf * (q.edg + q.curv * reach) && (sl > 0.0f) != plo;
@@ -413,7 +414,9 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
             if (!(dn > L && dn < H)) dn = 0.5f * (L + H);
             if (!(dn > L && dn < H)) break;  // the bracket is down to adjacent floats
             d = dn;
-            q = growth_f3_full(x0f + d, rd3f, kf, &tf, physics);
+            // with the bounds: where the locate stops here, they are the
+            // polish's slope bounds at mu and need no second evaluation
+            q = growth_f3_bounds(x0f + d, rd3f, kf, &tf, physics);
         }
     }
     S.mono = mono;
@@ -438,7 +441,7 @@ SDM_HD void fs_locate(FastSolve &S, float L, float H, bool plo, const ThermoF &t
     S.mu = mu;
     // f' at mu for the first Newton step (D_eff's variation included)
     const float xs = x0f + mu;
-    const GF qs = growth_f3_slope<CERT>(xs, rd3f, kf, &tf, physics);
+    const GF qs = CERT && mono && undecided ? q : growth_f3_slope<CERT>(xs, rd3f, kf, &tf, physics);
     const float dg = qs.dg;
     if (CERT) {
         S.es = dtp * (double)qs.edg;
@@ -1306,6 +1309,9 @@ constexpr int kStagedListRounds = 3;  // rounds over compacted lists before the 
 // super-droplets (measured on GB300: below that the fused kernel's single
 // launch wins; from it the chain, by 10-20 % in 3D)
 constexpr int64_t kStagedMinSd = int64_t(1) << 17;
+// round 0 of domains of at least 2^22 super-droplets regroups tiles of 1024
+// records (4 per thread); smaller lists keep 256, enough blocks to fill the SMs
+constexpr int64_t kStagedWideTileSd = int64_t(1) << 22;
 
 __global__ void k_cs_cells(const double *th, const double *rv, const double *rhod, int n_cells, double RH_max,
                            StagedCell *out) {
@@ -1391,34 +1397,42 @@ SDM_HD int vent_class(float x, const ThermoF &tf, int physics) {
     return y <= 5.9604645e-8f ? kel : y <= 0.015625f ? 2 : Re <= 1.0f ? 3 : 4;
 }
 
-template <bool FINISH>
+// RPT records per thread: the regrouping sorts tiles of 256 x RPT records,
+// so that fewer warps straddle two classes (for the large lists of round 0).
+template <bool FINISH, int RPT = 1>
 __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, int64_t rev_end,
                                                  StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
                                                  const StagedCell *cells, double dtp, int physics, double *x1,
                                                  DevStats *st) {
     constexpr int kKeys = 16;  // 3 kinds of record x 5 classes of evaluation, then the empty slots
+    constexpr unsigned kTile = 256 * RPT;  // blockDim.x == 256
     __shared__ unsigned s_warp[8], s_base, s_cnt[kKeys];
-    __shared__ uint16_t s_perm[256];
+    __shared__ uint16_t s_perm[kTile];
     const unsigned n = *n_in;
     SolveCounters cnt{0, 0, 0, 0};
     bool bad = false;
-    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    for (unsigned base = blockIdx.x * kTile; base < n; base += gridDim.x * kTile) {
         // the tile's records regrouped by the branches their evaluation
         // takes (the task, then growth_coef's), so that the lanes of a warp
         // run the same code; each record's arithmetic is unchanged
-        unsigned t = base + threadIdx.x;
-        int key = kKeys - 1;
-        if (t < n) {
-            const StagedRec &q = rev_end ? in[rev_end - 1 - t] : in[t];
-            if (q.task != kTaskNone) {
-                const bool g0 = q.task != kTaskPolish;
-                const int kind = !g0 ? 0 : q.task == kTaskG0Exact ? 1 : 2;
-                key = 5 * kind + vent_class((float)(g0 ? q.S.x0 : q.S.xk), cells[cell_of_sd[q.sd]].tf, physics);
-            }
-        }
+        int key[RPT];
+        unsigned rank[RPT];
         if (threadIdx.x < kKeys) s_cnt[threadIdx.x] = 0;
         __syncthreads();
-        const unsigned rank = atomicAdd(&s_cnt[key], 1u);
+#pragma unroll
+        for (int jj = 0; jj < RPT; ++jj) {
+            const unsigned t = base + jj * 256 + threadIdx.x;
+            key[jj] = kKeys - 1;
+            if (t < n) {
+                const StagedRec &q = rev_end ? in[rev_end - 1 - t] : in[t];
+                if (q.task != kTaskNone) {
+                    const bool g0 = q.task != kTaskPolish;
+                    const int kind = !g0 ? 0 : q.task == kTaskG0Exact ? 1 : 2;
+                    key[jj] = 5 * kind + vent_class((float)(g0 ? q.S.x0 : q.S.xk), cells[cell_of_sd[q.sd]].tf, physics);
+                }
+            }
+            rank[jj] = atomicAdd(&s_cnt[key[jj]], 1u);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned tot = 0;
@@ -1429,9 +1443,11 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
             }
         }
         __syncthreads();
-        s_perm[s_cnt[key] + rank] = (uint16_t)threadIdx.x;
+#pragma unroll
+        for (int jj = 0; jj < RPT; ++jj) s_perm[s_cnt[key[jj]] + rank[jj]] = (uint16_t)(jj * 256 + threadIdx.x);
         __syncthreads();
-        t = base + s_perm[threadIdx.x];
+      for (int jj = 0; jj < RPT; ++jj) {
+        const unsigned t = base + s_perm[jj * 256 + threadIdx.x];
         bool keep = false;
         StagedRec r;
         if (t < n) {
@@ -1487,6 +1503,7 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
         __syncthreads();
         if (keep) out[s_base + s_warp[w] + __popc(m & ((1u << lane) - 1u))] = r;
         __syncthreads();
+      }
     }
     const unsigned ne = __reduce_add_sync(0xffffffffu, (unsigned)cnt.euler);
     const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)cnt.fallback);
@@ -1563,10 +1580,17 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
         k_cs_start<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, dtp,
                                                                    c->oi.physics, rec[0], c->cs_x1, cnt, n_pol,
                                                                    (unsigned)n);
-        for (int part = 0; part < 2; ++part)
-            k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0, rec[1],
-                                                                 cnt + 1, cell_of_sd, cells, dtp, c->oi.physics,
-                                                                 c->cs_x1, c->dstats);
+        // round 0 regroups tiles of 1024 records where the lists are long
+        for (int part = 0; part < 2; ++part) {
+            if (n >= kStagedWideTileSd)
+                k_cs_eval<false, 4><<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0,
+                                                                        rec[1], cnt + 1, cell_of_sd, cells, dtp,
+                                                                        c->oi.physics, c->cs_x1, c->dstats);
+            else
+                k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[0], part ? n_pol : cnt, part ? n : 0,
+                                                                     rec[1], cnt + 1, cell_of_sd, cells, dtp,
+                                                                     c->oi.physics, c->cs_x1, c->dstats);
+        }
         for (int r = 1; r < kStagedListRounds; ++r)
             k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1],
                                                                  cnt + r + 1, cell_of_sd, cells, dtp, c->oi.physics,
