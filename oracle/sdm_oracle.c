@@ -13,8 +13,11 @@
  * marked "READING" below; the CUDA library follows the same readings.
  *
  * Functions whose exact formula the paper only cites (transition-regime
- * factors, ventilation, terminal velocity, viscosity) are parity unpinned
- * except for their limits: see orc_growth() and orc_vterm().
+ * factors, ventilation, terminal velocity, viscosity) are pinned against
+ * other published forms (Seinfeld & Pandis's Fuchs-Sutugin arrangement,
+ * Pruppacher & Klett's ventilation coefficient, tabulated air viscosity)
+ * and, for the fall speed, against Stokes' law and Gunn & Kinzer's
+ * measurements within 12 %: see orc_growth() and orc_vterm().
  *
  * The same source, compiled with -fopenmp, is the oracle's cell-parallel
  * timing variant (the paper's OpenMP back-end, Sec. 6): the "omp" pragmas
@@ -166,7 +169,8 @@ void orc_thermo_eval(double th, double rv, double rhod, double RH_max, orc_therm
 /* READING of Khvorostyanov & Curry (2002) for a sphere: Reynolds number as a
  * function of the Best number X, Re = delta0^2/4 (sqrt(1 + c1 sqrt(X)) - 1)^2
  * with c1 = 4 / (delta0^2 sqrt(C0)); it tends to Stokes' Re = X/24 for small
- * X.  Parity unpinned except for that Stokes limit. */
+ * X.  Pinned by that Stokes limit and by Gunn & Kinzer's (1949) measured
+ * fall speeds within 12 % (the fit approximates such measurements). */
 double orc_reynolds(double rw2, const orc_thermo *t)
 {
     double r = sqrt(rw2);
@@ -201,8 +205,10 @@ static double fuchs_sutugin(double Kn)
  *   D = D0 beta_M Sh/2, K = K0 beta_T Nu/2                (Sec. 5.1.3).
  * physics == 0 drops the corrections (beta = 1, Sh = Nu = 2).
  * READING: Sh = 1 + (1 + Re Sc)^(1/3) f(Re), Nu likewise with Pr, and
- * f = 1 for Re <= 1, Re^0.077 above (Clift et al. 1978); parity unpinned
- * except for the limits Kn -> 0 (beta -> 1) and Re -> 0 (Sh = Nu = 2). */
+ * f = 1 for Re <= 1, Re^0.077 above (Clift et al. 1978).  Pinned by the
+ * limits Kn -> 0 (beta -> 1) and Re -> 0 (Sh = Nu = 2), by Seinfeld &
+ * Pandis's arrangement of beta (Kn 0.08-4) and by Pruppacher & Klett's
+ * ventilation coefficient within 5 % (Re up to 170). */
 double orc_growth(double x, double rd3, double kappa, const orc_thermo *t, int physics)
 {
     double r = sqrt(x);
