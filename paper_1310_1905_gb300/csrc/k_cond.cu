@@ -134,11 +134,32 @@ SDM_HD float growth_f(float x, float rd3, float kappa, const ThermoF &t, int phy
     const float Deff = fdiv(1.0f, fdiv(1.0f, D) + fdiv(t.Dterm, K));
     const float c = 2.0f * Deff / (float)phys::rho_w;
     const float g = c * (t.rho_v_eff - rho_o);
-    // rounding of the difference's terms (a_w amplified where r ~ r_d) and
-    // of the D_eff factor, with a safety factor
+    // Error bound.  u = 2^-24; a correctly rounded FP32 operation or
+    // conversion errs by at most u (relative), the 2-ulp division fdiv by
+    // 4u, expf (2 ulps) by 4u, sqrtf (correctly rounded) by u, cbrtf (1 ulp)
+    // by 2u, powf (4 ulps) by 8u; to first order, relative errors add along
+    // a chain and scale by the logarithmic sensitivity of the result.
+    // - The point x = x0f + d errs by 2u (x0's conversion, the sum), r3 by
+    //   5u (x^1.5, the root, the product).
+    // - rho_v_eff: one conversion, u.
+    // - rho_o = rho_vs a_w e^(A/r): a_w = num/den moves with r3 by at most
+    //   kappa r3 rd3 / (num den) <= amp per unit relative change of r3 (num
+    //   and den move together), so 5u amp; the roundings of rd3 and of the
+    //   two differences, u (r3 + rd3)/|num| <= u amp and 2u; fdiv 4u: a_w
+    //   within (6 amp + 6) u.  A/r: A's conversion, the root, fdiv: 7u, so
+    //   e^(A/r) within 7u A/r + 4u.  rho_vs and two products: 3u.  In all
+    //   (13 + 6 amp + 7 A/r) u, inside the (16 + 8 amp + 8 A/r) u taken.
+    // - the factor c = 2 D_eff / rho_w: through X, e, s and Re (23u), the
+    //   cube roots (11u each), Re^0.077 (10u), Kn and the transition factors
+    //   (15u each), D and K (41u), D_eff (51u) and c (53u), inside the 64u
+    //   of |g| taken for it.
+    // The sign of f = d - dt' g taken from this value is then the one an
+    // FP64 evaluation at x0 + d gives wherever |f| clears the callers'
+    // margin (4u |d| for the rounding of d and of the difference, plus
+    // 4 dt' err).
     const float amp = fdiv(r3 + rd3, fmaxf(fabsf(num), 1e-37f));
     const float eps = 5.9604645e-8f;  // 2^-24
-    *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 4.0f * Ar)) + 64.0f * fabsf(g));
+    *err = eps * (c * (4.0f * t.rho_v_eff + rho_o * (16.0f + 8.0f * amp + 8.0f * Ar)) + 64.0f * fabsf(g));
     if (DG != kDgNone) {
         // 3 r^2 rd3 kappa / den^2 without squaring den (~1e-24 m^3 for 10 nm
         // droplets, whose square underflows FP32)
