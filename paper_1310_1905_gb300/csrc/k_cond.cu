@@ -1536,23 +1536,29 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
     }
 }
 
-// one warp per cell: eq. rhov_update with the new radii, in a fixed order
+// one warp per cell: eq. rhov_update with the new radii, in a fixed order.
+// r3[i] holds r_w^3 = x sqrt(x) of the super-droplet's current r_w^2 (set by
+// k_cs_cellmap, then by each update for the next substep), so each substep
+// takes one square root per super-droplet; fac[c] = -4 pi rho_w / (3 dV
+// rho_d), fixed through the call.
 __global__ void k_cs_update(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells,
-                            const double *x1, double *th, double *rv, const double *rhod, double dV, DevStats *st) {
+                            const double *x1, double *r3, const double *fac, double *th, double *rv,
+                            DevStats *st) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c64 >= n_cells) return;
     const int c = (int)c64, lane = threadIdx.x & 31;
     double sum = 0.0;
     for (uint32_t i = offset[c] + lane; i < offset[c + 1]; i += 32) {
         const unsigned long long N = s.N[i];
-        const double x0 = s.rw2[i], xn = x1[i];
-        if (N != 0) sum += (double)N * (xn * sqrt(xn) - x0 * sqrt(x0));
+        const double xn = x1[i], r3n = xn * sqrt(xn);
+        if (N != 0) sum += (double)N * (r3n - r3[i]);
+        r3[i] = r3n;
         s.rw2[i] = xn;
     }
     sum = warp_sum(sum);
     if (lane == 0) {
         const Thermo &t = cells[c].t;
-        const double drv = -4.0 * phys::pi * phys::rho_w / (3.0 * dV * rhod[c]) * sum;
+        const double drv = fac[c] * sum;
         const double rvn = t.rv + drv, thn = t.th + drv * t.dth_drv;
         rv[c] = rvn;
         th[c] = thn;
@@ -1560,11 +1566,19 @@ __global__ void k_cs_update(SdArrays s, const uint32_t *offset, int n_cells, con
     }
 }
 
-__global__ void k_cs_cellmap(const uint32_t *offset, int n_cells, uint32_t *cell_of_sd) {
+// once per call: the cell of every super-droplet, its r_w^3, and each
+// cell's factor of eq. rhov_update
+__global__ void k_cs_cellmap(SdArrays s, const uint32_t *offset, int n_cells, const double *rhod, double dV,
+                             uint32_t *cell_of_sd, double *r3, double *fac) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c64 >= n_cells) return;
     const int c = (int)c64;
-    for (uint32_t i = offset[c] + (threadIdx.x & 31); i < offset[c + 1]; i += 32) cell_of_sd[i] = (uint32_t)c;
+    for (uint32_t i = offset[c] + (threadIdx.x & 31); i < offset[c + 1]; i += 32) {
+        cell_of_sd[i] = (uint32_t)c;
+        const double x0 = s.rw2[i];
+        r3[i] = x0 * sqrt(x0);
+    }
+    if ((threadIdx.x & 31) == 0) fac[c] = -4.0 * phys::pi * phys::rho_w / (3.0 * dV * rhod[c]);
 }
 
 static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *launches) {
@@ -1575,7 +1589,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
         e = cudaMalloc(&c->cs_rec[0], sizeof(StagedRec) * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_rec[1], sizeof(StagedRec) * (size_t)n);
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_cell, sizeof(StagedCell) * (size_t)nc + 4 * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&c->cs_x1, 8 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&c->cs_x1, 16 * (size_t)n + 8 * (size_t)nc);  // x1, r_w^3, factors
         if (e == cudaSuccess) e = cudaMalloc(&c->cs_cnt, 4 * (kStagedListRounds + 3));
         if (e != cudaSuccess) return e;
     }
@@ -1585,7 +1599,9 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
     const double dtp = c->grid.dt / o.sstp_cond;
     const int64_t warps_threads = (int64_t)nc * 32;
     const int B = 128;
-    k_cs_cellmap<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->offset, nc, cell_of_sd);
+    double *r3 = c->cs_x1 + n, *fac = r3 + n;
+    k_cs_cellmap<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, c->rhod,
+                                                                 c->grid.dV, cell_of_sd, r3, fac);
     *launches = 1 + o.sstp_cond * (kStagedListRounds + 5);  // cells, start, 2 + (rounds - 1) + 1 evals, update
     int dev = 0, n_sm = 152;
     cudaGetDevice(&dev);
@@ -1620,7 +1636,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
         k_cs_eval<true><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, nullptr, nullptr, cell_of_sd,
                                                             cells, dtp, c->oi.physics, c->cs_x1, c->dstats);
         k_cs_update<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, c->cs_x1,
-                                                                    c->th, c->rv, c->rhod, c->grid.dV, c->dstats);
+                                                                    r3, fac, c->th, c->rv, c->dstats);
     }
     return cudaGetLastError();
 }
