@@ -330,6 +330,10 @@ struct FastSolve {
     int k;
     bool plo, undecided, mu_inside, pmu, have_slope, clamp;
     bool mono;  // certified solves: f proven strictly monotone on the bracket (one root: no replay)
+    // deferred bracket ends (staged layout): the ends whose sign needs the
+    // term-by-term FP64 residual (bits 0, 1 for a, b) and the decided signs
+    uint8_t pend;
+    bool pe0, pe1;
 };
 
 // The growth rate for the fast solve, one evaluation for both of its uses
@@ -520,6 +524,15 @@ SDM_HD double fs_replay(FastSolve &S, double r, const Thermo &t, const ThermoF &
 // the locate.  Returns true when the solve is finished (S.x1 set).  CERT: a
 // certified Newton step from x0 finishes it too.
 template <bool CERT>
+SDM_HD bool fs_after_ends(FastSolve &S, double g0, bool pa, bool pb, GF q0, const Thermo &t, const ThermoF &tf,
+                          double dtp, int physics, SolveCounters &cnt);
+
+// DEFER (staged layout): where an end's sign needs the term-by-term FP64
+// residual (fres_rare), the solve stops with that end in S.pend, the decided
+// signs in S.pe0, S.pe1 and g0 in S.x1, and returns false; fs_resume_ends
+// takes it from there in the next round, so that the few records that need
+// it share warps instead of holding up the others.
+template <bool CERT, bool DEFER = false>
 SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF &tf, double dtp, int physics,
                         SolveCounters &cnt) {
     const double x0 = S.x0;
@@ -538,6 +551,7 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
     const double b = x0 + fmax(2.0 * dtp * g0, 0.0);
     S.a = a;
     S.b = b;
+    if (DEFER) S.pend = 0;
     // the ends' signs; at x0 itself f = -dtp g0 exactly.  The sign of f at
     // x0 + d (d an FP32 increment) is computed in FP32 and trusted where |f|
     // exceeds its error bound (it is then the sign an FP64 evaluation gives).
@@ -575,11 +589,48 @@ SDM_HD bool fs_after_g0(FastSolve &S, double g0, const Thermo &t, const ThermoF 
             const float d = (float)(xe - x0);
             const GF q = growth_f3_call(x0f + d, rd3f, kf, &tf, physics);
             const float f = d - dtpf * q.g;
-            pe[e] = fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err
-                        ? f > 0.0f
-                        : fres_rare(xe, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
+            if (fabsf(f) > 2.4e-7f * fabsf(d) + 4.0f * dtpf * q.err) {
+                pe[e] = f > 0.0f;
+            } else if (DEFER) {
+                S.pend |= (uint8_t)(1 << e);
+                pe[e] = false;
+            } else {
+                pe[e] = fres_rare(xe, x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
+            }
         }
     }
+    if (DEFER && S.pend) {
+        S.pe0 = pe[0];
+        S.pe1 = pe[1];
+        S.x1 = g0;
+        return false;
+    }
+    return fs_after_ends<CERT>(S, g0, pe[0], pe[1], q0, t, tf, dtp, physics, cnt);
+}
+
+// The deferred ends' signs from the term-by-term FP64 residual, then the
+// rest of fs_after_g0.
+template <bool CERT>
+SDM_HD bool fs_resume_ends(FastSolve &S, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                           SolveCounters &cnt) {
+    bool pe[2] = {S.pe0, S.pe1};
+    for (int e = 0; e < 2; ++e)
+        if (S.pend & (1 << e)) pe[e] = fres_rare(e ? S.b : S.a, S.x0, S.rd3, S.kappa, &t, dtp, physics) > 0.0;
+    S.pend = 0;
+    GF q0;
+    if (CERT) q0 = growth_f3_slope<CERT>((float)S.x0, (float)S.rd3, (float)S.kappa, &tf, physics);
+    return fs_after_ends<CERT>(S, S.x1, pe[0], pe[1], q0, t, tf, dtp, physics, cnt);
+}
+
+// After the signs pa, pb of f at the bracket's ends a = S.a, b = S.b: the
+// Euler step, the bisection's first exit, or the setup of the polish (CERT:
+// q0, the FP32 slope and its bounds at x0, is given).
+template <bool CERT>
+SDM_HD bool fs_after_ends(FastSolve &S, double g0, bool pa, bool pb, GF q0, const Thermo &t, const ThermoF &tf,
+                          double dtp, int physics, SolveCounters &cnt) {
+    const double x0 = S.x0, a = S.a, b = S.b;
+    const float rd3f = (float)S.rd3, kf = (float)S.kappa, x0f = (float)x0;
+    const bool pe[2] = {pa, pb};
     if (pe[0] == pe[1]) {  // f keeps its strict sign: the Euler step
         cnt.euler++;
         S.x1 = 0.5 * (a + b);
@@ -1311,7 +1362,8 @@ static int launch_condense_mode(sdm_ctx *c, const sdm_opts &o, int lpc, int B) {
 // corrections in FP32 (each within 1e-12 of the bisection's root, like the
 // fused solve).  The solve state travels through HBM between the kernels,
 // which the FP64-bound fused kernel leaves idle.
-enum { kTaskNone = 0, kTaskG0Euler = 1, kTaskG0Tiny = 2, kTaskG0Exact = 3, kTaskPolish = 4 };
+enum { kTaskNone = 0, kTaskG0Euler = 1, kTaskG0Tiny = 2, kTaskG0Exact = 3, kTaskPolish = 4, kTaskG0End = 5 };
+// kTaskG0End: g(x0) done, a bracket end's sign deferred (fs_resume_ends)
 
 struct StagedRec {
     FastSolve S;
@@ -1425,7 +1477,7 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                                                  StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
                                                  const StagedCell *cells, double dtp, int physics, double *x1,
                                                  DevStats *st) {
-    constexpr int kKeys = 16;  // 3 kinds of record x 5 classes of evaluation, then the empty slots
+    constexpr int kKeys = 17;  // 3 kinds of record x 5 classes of evaluation, the deferred ends, the empty slots
     constexpr unsigned kTile = 256 * RPT;  // blockDim.x == 256
     __shared__ unsigned s_warp[8], s_base, s_cnt[kKeys];
     __shared__ uint16_t s_perm[kTile];
@@ -1446,7 +1498,9 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
             key[jj] = kKeys - 1;
             if (t < n) {
                 const StagedRec &q = rev_end ? in[rev_end - 1 - t] : in[t];
-                if (q.task != kTaskNone) {
+                if (q.task == kTaskG0End) {
+                    key[jj] = 15;
+                } else if (q.task != kTaskNone) {
                     const bool g0 = q.task != kTaskPolish;
                     const int kind = !g0 ? 0 : q.task == kTaskG0Exact ? 1 : 2;
                     key[jj] = 5 * kind + vent_class((float)(g0 ? q.S.x0 : q.S.xk), cells[cell_of_sd[q.sd]].tf, physics);
@@ -1478,8 +1532,13 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                 FastSolve &S = r.S;
                 bool done = false;
                 for (int k = 0; k < (FINISH ? kStagedRounds : 1) && !done; ++k) {
-                    const bool g0 = r.task != kTaskPolish;
                     cnt.evals++;
+                    if (r.task == kTaskG0End) {  // the deferred ends' FP64 residuals
+                        done = fs_resume_ends<true>(S, cl.t, cl.tf, dtp, physics, cnt);
+                        if (!done) r.task = kTaskPolish;
+                        continue;
+                    }
+                    const bool g0 = r.task != kTaskPolish;
                     double mag;
                     const double v = growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag);
                     if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
@@ -1487,7 +1546,9 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                         S.x1 = fs_euler(S, v, dtp);
                         done = true;
                     } else if (r.task == kTaskG0Exact) {
-                        done = fs_after_g0<true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
+                        done = fs_after_g0<true, true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
+                        if (!done) r.task = S.pend ? kTaskG0End : kTaskPolish;
+                        continue;
                     } else {
                         done = fs_after_polish<true>(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
                     }
