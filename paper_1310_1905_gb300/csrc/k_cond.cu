@@ -1400,7 +1400,7 @@ __global__ void k_cs_cells(const double *th, const double *rv, const double *rho
 // The records go to one list of n slots: those whose first FP64 evaluation
 // is g(x0) from the front (count n_g0), those that start their polish from
 // the back (count n_pol), so that round 0 runs each kind in warps of its own.
-__global__ void k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells, double dtp,
+__global__ void __launch_bounds__(128, 7) k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells, double dtp,
                            int physics, StagedRec *rec, double *x1, unsigned *n_g0, unsigned *n_pol,
                            unsigned n_sd) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
