@@ -232,7 +232,7 @@ SDM_HD double sqrt1pm1_small(double e) {
 // less than 2^-45 of its increment x1 - x0.  The staged solves take it; the
 // fused kernel's and the bisection's coefficient stays FP64 throughout.
 template <bool LITE = false>
-SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
+SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics, const ThermoF *tf = nullptr) {
     using namespace phys;
     double a = D0, b = K0, DM = 1.0, DT = 1.0;
     if (physics) {
@@ -241,11 +241,14 @@ SDM_HD Coef growth_coef(double rinv, double r3, const Thermo &t, int physics) {
         DM = 1.0 + c1 * KnM + c2 * KnM * KnM;
         DT = 1.0 + c1 * KnT + c2 * KnT * KnT;
         if (LITE) {
-            const float Xf = (float)t.cX * (float)r3;
+            // tf: the FP32 copies of cX, Sc and Pr (the same roundings as (float) here)
+            const float cXf = tf ? tf->cX : (float)t.cX, Scf = tf ? tf->Sc : (float)t.Sc;
+            const float Prf = tf ? tf->Pr : (float)t.Pr;
+            const float Xf = cXf * (float)r3;
             const float ef = (float)(4.0 / (delta0 * delta0 * sqrt(C0))) * sqrtf(Xf);
             const float sf = ef / (sqrtf(1.0f + ef) + 1.0f);
             const float Ref = (float)(delta0 * delta0 / 4.0) * sf * sf;
-            const float yS = Ref * (float)t.Sc, yN = Ref * (float)t.Pr;
+            const float yS = Ref * Scf, yN = Ref * Prf;
             if (fmaxf(yS, yN) <= 5.9604645e-8f) {  // 2^-24: (1 + y)^(1/3) - 1 = y/3 - y^2/9 + ...
                 const double Sh = 2.0 + (double)(yS * (0.33333333f - 0.11111111f * yS));
                 const double Nu = 2.0 + (double)(yN * (0.33333333f - 0.11111111f * yN));
@@ -336,6 +339,17 @@ struct FastSolve {
     bool pe0, pe1;
 };
 
+// 1/y from the FP32 reciprocal (within 2^-23) refined by two Newton
+// iterations (error squared each time, to FP64 rounding); the FP32 range is
+// checked, with the division outside it
+SDM_HD double rcp_refined(double y) {
+    const double ay = fabs(y);
+    if (!(ay > 1e-36 && ay < 1e36)) return 1.0 / y;
+    double r = (double)(1.0f / (float)y);
+    r = fma(r, fma(-y, r, 1.0), r);
+    return fma(r, fma(-y, r, 1.0), r);
+}
+
 // The growth rate for the fast solve, one evaluation for both of its uses
 // so that the solve has one copy of it.
 // exact = true: g(x0) for the bracket and the Euler step.  rho_v - rho_o,
@@ -353,7 +367,7 @@ struct FastSolve {
 //   terms, the rounding level the certified steps already allow for.
 template <bool LITE = false>
 SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const Thermo &t, int physics,
-                          double *mag) {
+                          double *mag, const ThermoF *tf = nullptr) {
     double r, rinv;
     if (exact && !LITE) {
         r = sqrt(x);
@@ -373,13 +387,17 @@ SDM_HD double growth_eval(double x, bool exact, double rd3, double kappa, const 
     } else {
         kel = exp(y);
     }
-    const Coef c = growth_coef<LITE>(rinv, r3, t, physics);
+    const Coef c = growth_coef<LITE>(rinv, r3, t, physics, tf);
     const double num = r3 - rd3, den = r3 - rd3 * (1.0 - kappa);
     if (exact) {
         *mag = 0.0;
         return c.n / c.d * (t.rho_v_eff - t.rho_vs * (num / den) * kel);
     }
-    const double q = c.n / (c.d * den), v = t.rho_v_eff * den, o = t.rho_vs * num * kel;
+    // LITE: 1/(c.d den) from the FP32 reciprocal and two FP64 Newton
+    // iterations (within an ulp or two of the quotient, inside the 16 ulps
+    // of the terms that the polish's certificate allows for g's rounding)
+    const double q = LITE ? c.n * rcp_refined(c.d * den) : c.n / (c.d * den);
+    const double v = t.rho_v_eff * den, o = t.rho_vs * num * kel;
     *mag = q * (v + fabs(o));
     return q * (v - o);
 }
@@ -914,7 +932,7 @@ __host__ __device__ double solve_rw2_fast(double x0, double rd3, double kappa, c
         const bool g0 = k == 0 && start != kStartPolish;
         cnt.evals++;
         double mag;
-        const double v = growth_eval<CERT>(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag);
+        const double v = growth_eval<CERT>(g0 ? x0 : S.xk, g0, rd3, kappa, t, physics, &mag, &tf);
         if (g0) {
             if (start == kStartExact) {
                 if (fs_after_g0<CERT>(S, v, t, tf, dtp, physics, cnt)) return S.x1;
@@ -1540,7 +1558,8 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                     }
                     const bool g0 = r.task != kTaskPolish;
                     double mag;
-                    const double v = growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag);
+                    const double v =
+                        growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag, &cl.tf);
                     if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
                         if (r.task == kTaskG0Euler) cnt.euler++;
                         S.x1 = fs_euler(S, v, dtp);
