@@ -1389,6 +1389,42 @@ struct StagedRec {
     int task;
 };
 
+// the first task of a solve from its start class
+SDM_HD int cs_task_of(int st) {
+    return st == kStartPolish  ? kTaskPolish
+           : st == kStartExact ? kTaskG0Exact
+           : st == kStartEuler ? kTaskG0Euler
+                               : kTaskG0Tiny;
+}
+
+// One round of a staged solve: one FP64 growth evaluation (or, for a
+// deferred bracket end, its term-by-term residual) and the step it feeds.
+// Returns true when the solve is finished (S.x1 set); task becomes the next
+// round's.  The host build runs the same sequence (tests/hostcheck).
+SDM_HD bool cs_step(int &task, FastSolve &S, const Thermo &t, const ThermoF &tf, double dtp, int physics,
+                    SolveCounters &cnt) {
+    cnt.evals++;
+    if (task == kTaskG0End) {  // the deferred ends' FP64 residuals
+        const bool done = fs_resume_ends<true>(S, t, tf, dtp, physics, cnt);
+        if (!done) task = kTaskPolish;
+        return done;
+    }
+    const bool g0 = task != kTaskPolish;
+    double mag;
+    const double v = growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, t, physics, &mag, &tf);
+    if (task == kTaskG0Euler || task == kTaskG0Tiny) {
+        if (task == kTaskG0Euler) cnt.euler++;
+        S.x1 = fs_euler(S, v, dtp);
+        return true;
+    }
+    if (task == kTaskG0Exact) {
+        const bool done = fs_after_g0<true, true>(S, v, t, tf, dtp, physics, cnt);
+        if (!done) task = S.pend ? kTaskG0End : kTaskPolish;
+        return done;
+    }
+    return fs_after_polish<true>(S, v, mag, t, tf, dtp, physics, cnt);
+}
+
 struct StagedCell {
     Thermo t;
     ThermoF tf;
@@ -1441,10 +1477,7 @@ __global__ void __launch_bounds__(128, 7) k_cs_start(SdArrays s, const uint32_t 
                 S.rd3 = s.rd3[i];
                 S.kappa = s.kappa[i];
                 const int st = fs_start<true>(S, tf, dtp, physics);
-                task = st == kStartPolish  ? kTaskPolish
-                       : st == kStartExact ? kTaskG0Exact
-                       : st == kStartEuler ? kTaskG0Euler
-                                           : kTaskG0Tiny;
+                task = cs_task_of(st);
             }
         }
         const unsigned mg = __ballot_sync(0xffffffffu, task != kTaskNone && task != kTaskPolish);
@@ -1549,30 +1582,8 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
                 const StagedCell &cl = cells[cell_of_sd[r.sd]];
                 FastSolve &S = r.S;
                 bool done = false;
-                for (int k = 0; k < (FINISH ? kStagedRounds : 1) && !done; ++k) {
-                    cnt.evals++;
-                    if (r.task == kTaskG0End) {  // the deferred ends' FP64 residuals
-                        done = fs_resume_ends<true>(S, cl.t, cl.tf, dtp, physics, cnt);
-                        if (!done) r.task = kTaskPolish;
-                        continue;
-                    }
-                    const bool g0 = r.task != kTaskPolish;
-                    double mag;
-                    const double v =
-                        growth_eval<true>(g0 ? S.x0 : S.xk, g0, S.rd3, S.kappa, cl.t, physics, &mag, &cl.tf);
-                    if (r.task == kTaskG0Euler || r.task == kTaskG0Tiny) {
-                        if (r.task == kTaskG0Euler) cnt.euler++;
-                        S.x1 = fs_euler(S, v, dtp);
-                        done = true;
-                    } else if (r.task == kTaskG0Exact) {
-                        done = fs_after_g0<true, true>(S, v, cl.t, cl.tf, dtp, physics, cnt);
-                        if (!done) r.task = S.pend ? kTaskG0End : kTaskPolish;
-                        continue;
-                    } else {
-                        done = fs_after_polish<true>(S, v, mag, cl.t, cl.tf, dtp, physics, cnt);
-                    }
-                    if (!done) r.task = kTaskPolish;
-                }
+                for (int k = 0; k < (FINISH ? kStagedRounds : 1) && !done; ++k)
+                    done = cs_step(r.task, S, cl.t, cl.tf, dtp, physics, cnt);
                 if (done) {
                     x1[r.sd] = S.x1;
                     bad |= !isfinite(S.x1);

@@ -16,9 +16,11 @@ Thermo cell_thermo(int64_t c, const double *th, const double *rv, const double *
 
 // solver: 0 the bisection (SDM_SOLVER_BISECT), 1 the fast solve
 // (SDM_SOLVER_FAST), 2 the FP32 solve of the mixed mode, 3 the fast solve
-// with certified Newton steps (the staged layout's).  counters: Euler
-// steps, exact-bisection fallbacks, FP64 growth evaluations, certified
-// settles.
+// with certified Newton steps (the staged layout's), 4 the staged layout's
+// sequence of rounds itself: its start (fs_start), then one cs_step per
+// round as the eval kernels take them, with the rare bracket ends deferred
+// to a round of their own.  counters: Euler steps, exact-bisection
+// fallbacks, FP64 growth evaluations, certified settles.
 extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const double *kappa, const int64_t *cell,
                          const double *th, const double *rv, const double *rhod, double RH_max, double dtp,
                          int physics, int solver, double *x1, int64_t *counters) {
@@ -34,6 +36,15 @@ extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const d
             x1[q] = solve_rw2_fast<false>(x0[q], rd3[q], kappa[q], t, tf, dtp, physics, cnt);
         } else if (solver == 3) {
             x1[q] = solve_rw2_fast<true>(x0[q], rd3[q], kappa[q], t, tf, dtp, physics, cnt);
+        } else if (solver == 4) {
+            FastSolve S;
+            S.x0 = x0[q];
+            S.rd3 = rd3[q];
+            S.kappa = kappa[q];
+            int task = cs_task_of(fs_start<true>(S, tf, dtp, physics));
+            bool done = false;
+            for (int k = 0; k < kStagedRounds && !done; ++k) done = cs_step(task, S, t, tf, dtp, physics, cnt);
+            x1[q] = done ? S.x1 : -1.0;
         } else {
             solve_rw2_f32(x0[q], rd3[q], kappa[q], tf, (float)dtp, physics, &x1[q], cnt);
         }

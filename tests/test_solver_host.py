@@ -72,6 +72,20 @@ def test_fast_solve_is_the_bisection_within_1e12(states, solver):
     assert (certified > n // 100) == (solver == 3)
 
 
+def test_staged_rounds_are_the_certified_solve(states):
+    """The staged layout's per-record sequence (the start, then one round
+    per FP64 evaluation, bracket ends that need the term-by-term residual
+    deferred to a round of their own) gives the certified solve's result bit
+    for bit: the deferral moves work between rounds, never its arithmetic."""
+    n = 0
+    for args in states[::3]:
+        a, _ = hostcheck.solve(*args, solver=3)
+        b, _ = hostcheck.solve(*args, solver=4)
+        assert np.array_equal(a, b), f"{(a != b).sum()} of {a.size} differ"
+        n += a.size
+    assert n > 100_000
+
+
 def test_host_bisection_is_the_oracle_bisection(states):
     """The library's bisection and the oracle's take the same halvings: equal
     to rounding of the growth rate's terms (the library's thermodynamics
