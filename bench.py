@@ -80,11 +80,11 @@ COND_FP64 = {
                                           dram_bytes_per_sd=331.62e6 / 8388608, fp64_pipe_active=0.7364,
                                           capture="3D updraft at 64^3 cells (8.4 M SDs), one launch; traffic "
                                                   "scaled by the SDs of a launch"),
-    ("icmw_2d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=313.20,
-                                        dram_bytes_per_sd=5063.8, fp64_pipe_active=0.380,
+    ("icmw_2d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=312.37,
+                                        dram_bytes_per_sd=5060.9, fp64_pipe_active=0.381,
                                         capture="2D case, 360 000 SDs, one call (81 launches)"),
-    ("updraft_3d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=302.36,
-                                           dram_bytes_per_sd=6654.5, fp64_pipe_active=0.588,
+    ("updraft_3d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=301.40,
+                                           dram_bytes_per_sd=6655.5, fp64_pipe_active=0.591,
                                            capture="3D updraft, 32x32x128 columns (4.2 M SDs), one call (81 "
                                                    "launches); traffic scaled by the SDs of a call"),
 }
