@@ -1436,8 +1436,9 @@ constexpr int kStagedListRounds = 3;  // rounds over compacted lists before the 
 // super-droplets (measured on GB300: below that the fused kernel's single
 // launch wins; from it the chain, by 10-20 % in 3D)
 constexpr int64_t kStagedMinSd = int64_t(1) << 17;
-// round 0 of domains of at least 2^22 super-droplets regroups tiles of 1024
-// records (4 per thread); smaller lists keep 256, enough blocks to fill the SMs
+// the rounds over lists of domains of at least 2^22 super-droplets regroup
+// tiles of 1024 records (4 per thread); smaller lists keep 256, enough
+// blocks to fill the SMs
 constexpr int64_t kStagedWideTileSd = int64_t(1) << 22;
 
 __global__ void k_cs_cells(const double *th, const double *rv, const double *rhod, int n_cells, double RH_max,
@@ -1719,10 +1720,16 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
                                                                      rec[1], cnt + 1, cell_of_sd, cells, dtp,
                                                                      c->oi.physics, c->cs_x1, c->dstats);
         }
-        for (int r = 1; r < kStagedListRounds; ++r)
-            k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1],
-                                                                 cnt + r + 1, cell_of_sd, cells, dtp, c->oi.physics,
-                                                                 c->cs_x1, c->dstats);
+        for (int r = 1; r < kStagedListRounds; ++r) {
+            if (n >= kStagedWideTileSd)
+                k_cs_eval<false, 4><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1],
+                                                                        cnt + r + 1, cell_of_sd, cells, dtp,
+                                                                        c->oi.physics, c->cs_x1, c->dstats);
+            else
+                k_cs_eval<false><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, rec[(r + 1) & 1],
+                                                                     cnt + r + 1, cell_of_sd, cells, dtp,
+                                                                     c->oi.physics, c->cs_x1, c->dstats);
+        }
         const int r = kStagedListRounds;
         k_cs_eval<true><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, nullptr, nullptr, cell_of_sd,
                                                             cells, dtp, c->oi.physics, c->cs_x1, c->dstats);
