@@ -1523,7 +1523,8 @@ SDM_HD int vent_class(float x, const ThermoF &tf, int physics) {
 }
 
 // RPT records per thread: the regrouping sorts tiles of 256 x RPT records,
-// so that fewer warps straddle two classes (for the large lists of round 0).
+// so that fewer warps straddle two classes (for the long lists of large
+// domains).
 template <bool FINISH, int RPT = 1>
 __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsigned *n_in, int64_t rev_end,
                                                  StagedRec *out, unsigned *n_out, const uint32_t *cell_of_sd,
@@ -1537,9 +1538,9 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
     SolveCounters cnt{0, 0, 0, 0};
     bool bad = false;
     for (unsigned base = blockIdx.x * kTile; base < n; base += gridDim.x * kTile) {
-        // the tile's records regrouped by the branches their evaluation
-        // takes (the task, then growth_coef's), so that the lanes of a warp
-        // run the same code; each record's arithmetic is unchanged
+        // the tile's records regrouped by what their round takes (the
+        // record's kind, then the branches of growth_eval), so that the lanes
+        // of a warp run the same code; each record's arithmetic is unchanged
         int key[RPT];
         unsigned rank[RPT];
         if (threadIdx.x < kKeys) s_cnt[threadIdx.x] = 0;
