@@ -233,7 +233,11 @@ sdm_status sdm_step_async(sdm_ctx *ctx, const sdm_opts *opts);
 
 /* Wait at most timeout_s seconds (< 0: no limit) for the context's stream.
  * rainfall_out (nullable) receives the accumulated rainfall [kg] (the paper's
- * step_async return value).  SDM_ETIMEOUT leaves the work in flight. */
+ * step_async return value).  SDM_ETIMEOUT leaves the work in flight.
+ * SDM_ENOTSUP if a cell held more than 8192 super-droplets in a context whose
+ * initial cells hold at most 8192 (such a context reserves no scratch for
+ * larger cells; one initialised with larger cells reserves 48 bytes per
+ * super-droplet and pairs any cell). */
 sdm_status sdm_wait(sdm_ctx *ctx, double timeout_s, double *rainfall_out);
 
 /* ---- the kinematic framework's Eulerian component (Sec. 2.1-2.2) --------

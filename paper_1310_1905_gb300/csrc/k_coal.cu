@@ -435,11 +435,15 @@ __device__ void block_sort(unsigned long long *key, unsigned long long *pk, int 
     }
 }
 
+// huge (may be null): scratch for cells above kBigCellCap, three arrays of
+// 2 n_sd records (a cell at twice its offset, so that the power-of-two
+// padding of one cell never reaches the next); those cells take the same
+// steps on global memory, slower but with the same results
 __global__ void __launch_bounds__(kBigBlock)
     k_coal_block(SdArrays src, SdArrays dst, const uint32_t *offset, const uint32_t *perm,
-                 const double *amb, CoalParams p, const uint32_t *bigcells, DevStats *st) {
+                 const double *amb, CoalParams p, const uint32_t *bigcells, DevStats *st,
+                 unsigned long long *huge, int64_t n_sd) {
     extern __shared__ unsigned long long smem[];
-    unsigned long long *skey = smem, *spk = smem + kBigCellCap, *sacc = smem + 2 * kBigCellCap;
     __shared__ int s_m;
     __shared__ unsigned long long s_cnt[4];
     __shared__ unsigned long long s_maxp;
@@ -451,9 +455,15 @@ __global__ void __launch_bounds__(kBigBlock)
         const int c = (int)bigcells[bi];
         const uint32_t beg = offset[c];
         const int n = (int)(offset[c + 1] - beg);
+        unsigned long long *skey = smem, *spk = smem + kBigCellCap, *sacc = smem + 2 * kBigCellCap;
         if (n > kBigCellCap) {
-            if (threadIdx.x == 0) atomicOr(&st->flags, kFlagBigCell);
-            continue;
+            if (!huge) {
+                if (threadIdx.x == 0) atomicOr(&st->flags, kFlagBigCell);
+                continue;
+            }
+            skey = huge + 2 * (int64_t)beg;
+            spk = huge + 2 * n_sd + 2 * (int64_t)beg;
+            sacc = huge + 4 * n_sd + 2 * (int64_t)beg;
         }
         int npow2 = 1;
         while (npow2 < n) npow2 <<= 1;
@@ -645,7 +655,7 @@ cudaError_t launch_coalesce(sdm_ctx *c, const sdm_opts &o, bool coal) {
     int blocks = nsm > 0 ? nsm : 152;
     if (blocks > c->grid.n_cells) blocks = c->grid.n_cells;
     k_coal_block<<<blocks, kBigBlock, smem, c->stream>>>(src, dst, c->offset, c->perm, c->amb, p,
-                                                         c->bigcells, c->dstats);
+                                                         c->bigcells, c->dstats, c->huge, c->n_sd);
     return cudaGetLastError();
 }
 

@@ -221,6 +221,7 @@ void free_ctx(sdm_ctx *c) {
     cudaFree(c->xch_tmp);
     cudaFree(c->offset);
     cudaFree(c->bigcells);
+    cudaFree(c->huge);
     cudaFree(c->th);
     cudaFree(c->rv);
     cudaFree(c->rhod);
@@ -296,7 +297,8 @@ sdm_status check_flags(sdm_ctx *c, unsigned flags) {
     if (flags & kFlagNumeric)
         return fail(c, SDM_ENUMERIC, "a kernel produced a non-finite radius or field value");
     if (flags & kFlagBigCell)
-        return fail(c, SDM_ENOTSUP, "a grid cell holds more than 8192 super-droplets");
+        return fail(c, SDM_ENOTSUP, "a grid cell holds more than 8192 super-droplets and the context has no "
+                                    "scratch for such cells (its initial cells hold at most 8192)");
     return SDM_OK;
 }
 
@@ -468,6 +470,7 @@ sdm_status sdm_init(const sdm_opts_init *oi, sdm_arr th, sdm_arr rv, sdm_arr rho
     if (e == cudaSuccess) e = dalloc(&c->count, nc + 1);
     if (e == cudaSuccess) e = dalloc(&c->offset, nc + 1);
     if (e == cudaSuccess) e = dalloc(&c->bigcells, nc);
+    if (e == cudaSuccess && (int64_t)c->G * c->oi.sd_conc > kBigCellCap) e = dalloc(&c->huge, 6 * n);
     if (e == cudaSuccess) e = dalloc(&c->th, nc);
     if (e == cudaSuccess) e = dalloc(&c->rv, nc);
     if (e == cudaSuccess) e = dalloc(&c->rhod, nc);

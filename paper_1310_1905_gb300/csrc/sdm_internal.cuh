@@ -326,6 +326,10 @@ struct sdm_ctx {
     int cur = 0;
     uint32_t *newcell = nullptr, *slot = nullptr, *perm = nullptr;
     uint32_t *count = nullptr, *offset = nullptr, *bigcells = nullptr;
+    // coalescence scratch for cells above kBigCellCap (keys, pair words and
+    // accept draws, 2 n_sd each, a cell at twice its offset): allocated where
+    // the initial cells are that large
+    unsigned long long *huge = nullptr;
     double *th = nullptr, *rv = nullptr, *rhod = nullptr, *amb = nullptr, *outbuf = nullptr;
     double *rhoC[3] = {nullptr, nullptr, nullptr};
     uint32_t *scan_tmp = nullptr;
