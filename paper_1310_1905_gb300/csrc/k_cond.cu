@@ -1450,14 +1450,14 @@ __global__ void k_cs_cells(const double *th, const double *rv, const double *rho
     out[c].tf = to_float(t);
 }
 
-// one warp per cell: every super-droplet's FP32 start; the record at its
-// storage index (round 0 takes every index)
+// one warp per cell: every super-droplet's FP32 start, from x0src, r_w^2 at
+// the substep's start (the state's at the first substep, then x1)
 // The records go to one list of n slots: those whose first FP64 evaluation
 // is g(x0) from the front (count n_g0), those that start their polish from
 // the back (count n_pol), so that round 0 runs each kind in warps of its own.
 __global__ void __launch_bounds__(128, 7) k_cs_start(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells, double dtp,
                            int physics, StagedRec *rec, double *x1, unsigned *n_g0, unsigned *n_pol,
-                           unsigned n_sd) {
+                           unsigned n_sd, const double *x0src) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int c = (int)c64, lane = threadIdx.x & 31;
     const bool live = c64 < n_cells;
@@ -1470,7 +1470,7 @@ __global__ void __launch_bounds__(128, 7) k_cs_start(SdArrays s, const uint32_t 
         int task = kTaskNone;
         FastSolve S;
         if (i < end) {
-            const double x0 = s.rw2[i];
+            const double x0 = x0src[i];
             if (s.N[i] == 0) {
                 x1[i] = x0;
             } else {
@@ -1636,7 +1636,7 @@ __global__ void __launch_bounds__(256) k_cs_eval(const StagedRec *in, const unsi
 // rho_d), fixed through the call.
 __global__ void k_cs_update(SdArrays s, const uint32_t *offset, int n_cells, const StagedCell *cells,
                             const double *x1, double *r3, const double *fac, double *th, double *rv,
-                            DevStats *st) {
+                            DevStats *st, bool last) {
     const int64_t c64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c64 >= n_cells) return;
     const int c = (int)c64, lane = threadIdx.x & 31;
@@ -1646,7 +1646,7 @@ __global__ void k_cs_update(SdArrays s, const uint32_t *offset, int n_cells, con
         const double xn = x1[i], r3n = xn * sqrt(xn);
         if (N != 0) sum += (double)N * (r3n - r3[i]);
         r3[i] = r3n;
-        s.rw2[i] = xn;
+        if (last) s.rw2[i] = xn;  // earlier substeps' r_w^2 stay in x1, where the next start reads them
     }
     sum = warp_sum(sum);
     if (lane == 0) {
@@ -1709,7 +1709,7 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
         if (e != cudaSuccess) return e;
         k_cs_start<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, dtp,
                                                                    c->oi.physics, rec[0], c->cs_x1, cnt, n_pol,
-                                                                   (unsigned)n);
+                                                                   (unsigned)n, sub ? c->cs_x1 : c->buf[c->cur].rw2);
         // round 0 regroups tiles of 1024 records where the lists are long
         for (int part = 0; part < 2; ++part) {
             if (n >= kStagedWideTileSd)
@@ -1735,7 +1735,8 @@ static cudaError_t launch_condense_staged(sdm_ctx *c, const sdm_opts &o, int *la
         k_cs_eval<true><<<eval_blocks, 256, 0, c->stream>>>(rec[r & 1], cnt + r, 0, nullptr, nullptr, cell_of_sd,
                                                             cells, dtp, c->oi.physics, c->cs_x1, c->dstats);
         k_cs_update<<<grid_for(warps_threads, B), B, 0, c->stream>>>(c->buf[c->cur], c->offset, nc, cells, c->cs_x1,
-                                                                    r3, fac, c->th, c->rv, c->dstats);
+                                                                    r3, fac, c->th, c->rv, c->dstats,
+                                                                    sub == o.sstp_cond - 1);
     }
     return cudaGetLastError();
 }
