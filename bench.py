@@ -84,7 +84,7 @@ COND_FP64 = {
                                         dram_bytes_per_sd=5060.9, fp64_pipe_active=0.381,
                                         capture="2D case, 360 000 SDs, one call (81 launches)"),
     ("updraft_3d", "fp64", "staged"): dict(kernel="condensation chain (k_cs_*)", flops_per_sd_substep=301.30,
-                                           dram_bytes_per_sd=6659.1, fp64_pipe_active=0.584,
+                                           dram_bytes_per_sd=6609.1, fp64_pipe_active=0.584,
                                            capture="3D updraft, 32x32x128 columns (4.2 M SDs), one call (81 "
                                                    "launches); traffic scaled by the SDs of a call"),
 }
