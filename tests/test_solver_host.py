@@ -2,7 +2,8 @@
 kernels' own source, tests/hostcheck) against the oracle's bisection of the
 paper's implicit growth equation (Sec. 5.1.3, eq. rw2_implicit), solve by
 solve, along oracle trajectories of the 2D case (eddy transport of theta
-and r_v, sedimentation and coalescence between the steps).
+and r_v, sedimentation and coalescence between the steps) and of columns of
+the 3D updraft.
 
 On the CPU both sides take exp, pow and log from the same math library, so
 these tests isolate the solver's logic: its FP32 sign decisions under error
@@ -84,6 +85,53 @@ def test_staged_rounds_are_the_certified_solve(states):
         assert np.array_equal(a, b), f"{(a != b).sum()} of {a.size} differ"
         n += a.size
     assert n > 100_000
+
+
+def trajectory_3d(steps=25, seed=0):
+    """As trajectory(), along a run of 4 x 4 x 128 columns of the 3D updraft
+    (the full height: haze below, activation near cloud base, cloud above)."""
+    w = workloads.updraft_3d(nx=4, ny=4, nz=128, seed=seed)
+    o = oracle.Oracle(w.cfg, omp=True)
+    o.init(w.th, w.rv, w.rhod)
+    dtp = w.cfg["dt"] / w.opts["sstp_cond"]
+    c = w.cfg
+    for _ in range(steps):
+        o.euler_step(w.rhoCx, w.rhoCy, w.rhoCz)
+        s = o.state
+        live = s.N > 0
+        i = np.clip(np.floor(s.x / c["dx"]).astype(np.int64), 0, c["nx"] - 1)
+        j = np.clip(np.floor(s.y / c["dy"]).astype(np.int64), 0, c["ny"] - 1)
+        k = np.clip(np.floor(s.z / c["dz"]).astype(np.int64), 0, c["nz"] - 1)
+        cell = (i * c["ny"] + j) * c["nz"] + k
+        yield (s.rw2[live].copy(), s.rd3[live].copy(), s.kappa[live].copy(), cell[live], o.th.copy(), o.rv.copy(),
+               o.rhod, dtp)
+        o.step_sync(w.opts)
+        o.step_async(w.opts, w.rhoCx, w.rhoCy, w.rhoCz)
+
+
+def test_certified_solve_along_a_3d_trajectory():
+    """The staged layout's solve along the 3D updraft: every solve within
+    1e-12 of the oracle's bisection, about 1.2 FP64 growth evaluations per
+    solve, most settled by a certified Newton step; and the staged rounds
+    give the same results bit for bit."""
+    hostcheck.build()
+    n = worst = evals = certified = 0
+    for q, args in enumerate(trajectory_3d()):
+        ref = oracle.solve_batch(*args)
+        got, c = hostcheck.solve(*args, solver=3)
+        rel = np.abs(got - ref) / ref
+        assert (rel <= 1e-12).all(), f"{(rel > 1e-12).sum()} solves differ by more than 1e-12; worst {rel.max():.3e}"
+        n += len(ref)
+        worst = max(worst, rel.max())
+        evals += c["evals"]
+        certified += c["certified"]
+        if q % 5 == 0:
+            assert np.array_equal(got, hostcheck.solve(*args, solver=4)[0])
+    print(f"3D: {n} solves, worst relative difference {worst:.2e}, {evals / n:.3f} FP64 growth evaluations per "
+          f"solve, {certified / n:.1%} certified settles")
+    assert n > 1_000_000
+    assert evals / n < 1.5
+    assert certified > n // 2
 
 
 def test_host_bisection_is_the_oracle_bisection(states):
