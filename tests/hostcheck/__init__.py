@@ -62,6 +62,20 @@ def solve(x0, rd3, kappa, cell, th, rv, rhod, dtp, solver=1, RH_max=44.0, physic
     return out, dict(euler=int(cnt[0]), fallback=int(cnt[1]), evals=int(cnt[2]), certified=int(cnt[3]))
 
 
+def staged_stats(x0, rd3, kappa, cell, th, rv, rhod, dtp, RH_max=44.0, physics=1):
+    """Start classes (polish, Euler, tiny, exact) and deferred bracket ends of
+    the staged sequence."""
+    x0, rd3, kappa, th, rv, rhod = _prep(x0, rd3, kappa, th, rv, rhod)
+    cell = np.ascontiguousarray(cell, np.int64)
+    out = np.zeros(5, np.int64)
+    L = lib()
+    L.hc_staged_stats.argtypes = [C.c_int64] + [C.POINTER(C.c_double)] * 3 + [C.POINTER(C.c_int64)] + \
+        [C.POINTER(C.c_double)] * 3 + [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int64)]
+    L.hc_staged_stats(len(x0), _d(x0), _d(rd3), _d(kappa), cell.ctypes.data_as(C.POINTER(C.c_int64)), _d(th), _d(rv),
+                      _d(rhod), RH_max, dtp, physics, out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return dict(polish=int(out[0]), euler=int(out[1]), tiny=int(out[2]), exact=int(out[3]), deferred_ends=int(out[4]))
+
+
 def growth(x, rd3, kappa, cell, th, rv, rhod, RH_max=44.0, physics=1):
     x, rd3, kappa, th, rv, rhod = _prep(x, rd3, kappa, th, rv, rhod)
     cell = np.ascontiguousarray(cell, np.int64)

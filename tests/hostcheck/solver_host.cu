@@ -55,6 +55,33 @@ extern "C" void hc_solve(int64_t n, const double *x0, const double *rd3, const d
     counters[3] = cnt.certified;
 }
 
+// The staged sequence's statistics: stats[0..3] the start classes
+// (kStartPolish, kStartEuler, kStartTiny, kStartExact), stats[4] the
+// records whose bracket end waited for a round of its own (kTaskG0End).
+extern "C" void hc_staged_stats(int64_t n, const double *x0, const double *rd3, const double *kappa,
+                                const int64_t *cell, const double *th, const double *rv, const double *rhod,
+                                double RH_max, double dtp, int physics, int64_t *stats) {
+    for (int k = 0; k < 5; ++k) stats[k] = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        const Thermo t = cell_thermo(cell[q], th, rv, rhod, RH_max);
+        const ThermoF tf = to_float(t);
+        SolveCounters cnt{0, 0, 0, 0};
+        FastSolve S;
+        S.x0 = x0[q];
+        S.rd3 = rd3[q];
+        S.kappa = kappa[q];
+        const int st = fs_start<true>(S, tf, dtp, physics);
+        stats[st]++;
+        int task = cs_task_of(st);
+        bool done = false;
+        for (int k = 0; k < kStagedRounds && !done; ++k) {
+            const int before = task;
+            done = cs_step(task, S, t, tf, dtp, physics, cnt);
+            if (task == kTaskG0End && before != kTaskG0End) stats[4]++;
+        }
+    }
+}
+
 // The FP32 growth rate with its error bound, and the FP64 one, at x.
 extern "C" void hc_growth(int64_t n, const double *x, const double *rd3, const double *kappa, const int64_t *cell,
                           const double *th, const double *rv, const double *rhod, double RH_max, int physics,

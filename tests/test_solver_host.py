@@ -116,6 +116,7 @@ def test_certified_solve_along_a_3d_trajectory():
     give the same results bit for bit."""
     hostcheck.build()
     n = worst = evals = certified = 0
+    cls = dict(polish=0, euler=0, tiny=0, exact=0, deferred_ends=0)
     for q, args in enumerate(trajectory_3d()):
         ref = oracle.solve_batch(*args)
         got, c = hostcheck.solve(*args, solver=3)
@@ -127,11 +128,17 @@ def test_certified_solve_along_a_3d_trajectory():
         certified += c["certified"]
         if q % 5 == 0:
             assert np.array_equal(got, hostcheck.solve(*args, solver=4)[0])
+        for key, v in hostcheck.staged_stats(*args).items():
+            cls[key] += v
     print(f"3D: {n} solves, worst relative difference {worst:.2e}, {evals / n:.3f} FP64 growth evaluations per "
           f"solve, {certified / n:.1%} certified settles")
+    m = sum(cls[key] for key in ("polish", "euler", "tiny", "exact"))
+    print("start classes:", {key: f"{v / m:.2%}" for key, v in cls.items()})
     assert n > 1_000_000
     assert evals / n < 1.5
     assert certified > n // 2
+    assert cls["polish"] > 0.6 * m and 0.1 * m < cls["exact"] < 0.4 * m  # most solves start from the FP32 locate
+    assert 0 < cls["deferred_ends"] < 0.02 * m  # the deferred bracket ends are rare
 
 
 def test_host_bisection_is_the_oracle_bisection(states):
